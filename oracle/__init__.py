@@ -1,0 +1,187 @@
+"""CPU oracle for the binned 3pCF / 4pCF counts (test infrastructure only).
+
+A plain, slow, obviously correct CPU implementation of the paper's
+definitions (graph of Sec. 2.1, enumeration of Sec. 2.2, merge-walk of
+Sec. 3.1, three-way walk of Eq. threeway, parity of Sec. 3.2 / Eq. volume,
+disconnected term of Sec. 3.3 / Eq. disc). It lives in ``gs_oracle.cpp`` and
+is loaded here with ctypes.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The CUDA library never uses it, and
+it shares no code with the CUDA library: only the seeded input generators in
+``catalogs`` serve both.
+
+Every parity claim of the GPU path rests on this module, so its functions
+are pinned by independent checks in ``tests/test_oracle_*.py``: brute force
+over all tuples on tiny inputs, networkx clique enumeration, the Burnside
+orbit counts, the Poisson closed form, mirror and rotation invariances and
+the paper's parity injection test.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "_build", "libgs_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C++ compiler (no GPU involved)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-pthread",
+               "-ffp-contract=off", "-o", tmp, _SRC]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    ci = ctypes.c_int
+    lib.or_quantize.argtypes = [P, i64, i64, ci, P]
+    lib.or_quantize.restype = ci
+    lib.or_graph_build.argtypes = [P, i64, i64, P, ci, ci, ci]
+    lib.or_graph_build.restype = P
+    lib.or_graph_num_edges.argtypes = [P]
+    lib.or_graph_num_edges.restype = i64
+    lib.or_graph_export.argtypes = [P, P, P, P]
+    lib.or_graph_export.restype = None
+    lib.or_graph_free.argtypes = [P]
+    lib.or_graph_free.restype = None
+    lib.or_num_configs.argtypes = [ci, ci]
+    lib.or_num_configs.restype = i64
+    lib.or_config_bins.argtypes = [ci, ci, i64, P, P]
+    lib.or_config_bins.restype = ci
+    lib.or_count_3pcf.argtypes = [P, P, P, P, i64, i64, ci]
+    lib.or_count_3pcf.restype = ci
+    lib.or_count_4pcf.argtypes = [P, P, P, P, P, P, ci]
+    lib.or_count_4pcf.restype = ci
+    lib.or_pairs.argtypes = [P, P, P, P]
+    lib.or_pairs.restype = ci
+    lib.or_disconnected.argtypes = [P, P, P, P, P, P]
+    lib.or_disconnected.restype = ci
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def quantize(pos, box_u: int, periodic: bool) -> np.ndarray:
+    """Float positions (h^-1 Mpc) -> int32 lattice coordinates (N, 3)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = np.empty(pos.shape, dtype=np.int32)
+    st = _load().or_quantize(_ptr(pos), pos.shape[0], int(box_u), int(bool(periodic)), _ptr(out))
+    if st != 0:
+        raise ValueError("coordinate outside the open box")
+    return out
+
+
+def num_configs(npoint: int, nb: int) -> int:
+    return int(_load().or_num_configs(int(npoint), int(nb)))
+
+
+def config_bins(npoint: int, nb: int, idx: int):
+    bins = np.zeros(6, dtype=np.uint8)
+    chiral = ctypes.c_int(0)
+    st = _load().or_config_bins(int(npoint), int(nb), int(idx), _ptr(bins), ctypes.byref(chiral))
+    if st != 0:
+        raise IndexError(idx)
+    return tuple(int(b) for b in bins[:npoint * (npoint - 1) // 2]), bool(chiral.value)
+
+
+class Graph:
+    """Full sorted adjacency (both directions) in the caller's labels."""
+
+    def __init__(self, xyz, box_u: int, edges_u, method: str = "grid", nthreads: int | None = None):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+        self.n = self.xyz.shape[0]
+        self.box_u = int(box_u)
+        self.edges_u = np.ascontiguousarray(edges_u, dtype=np.int64)
+        self.nb = len(self.edges_u) - 1
+        self.nthreads = nthreads or default_threads()
+        m = {"brute": 0, "grid": 1}[method]
+        self._h = _load().or_graph_build(_ptr(self.xyz), self.n, self.box_u, _ptr(self.edges_u),
+                                         self.nb, m, self.nthreads)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_graph_free(h)
+            self._h = None
+
+    def export(self):
+        """(ptr int64[N+1], nbr int32[E], bin uint8[E]) with sorted rows."""
+        e = _load().or_graph_num_edges(self._h)
+        ptr = np.empty(self.n + 1, dtype=np.int64)
+        nbr = np.empty(e, dtype=np.int32)
+        b = np.empty(e, dtype=np.uint8)
+        _load().or_graph_export(self._h, _ptr(ptr), _ptr(nbr), _ptr(b))
+        return ptr, nbr, b
+
+    def count_3pcf(self, w=None, hub_lo: int = 0, hub_hi: int = -1):
+        nc = num_configs(3, self.nb)
+        counts = np.zeros(nc, dtype=np.uint64)
+        wsum = np.zeros(nc, dtype=np.float64) if w is not None else None
+        wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        st = _load().or_count_3pcf(self._h, _ptr(wa), _ptr(counts), _ptr(wsum), int(hub_lo),
+                                   int(hub_hi), self.nthreads)
+        if st != 0:
+            raise ValueError(f"oracle 3pCF failed ({st})")
+        return (counts, wsum) if w is not None else counts
+
+    def count_4pcf(self, w=None):
+        """Returns (even u64, odd i64) or, with weights, (even, odd, weven, wodd)."""
+        nc = num_configs(4, self.nb)
+        even = np.zeros(nc, dtype=np.uint64)
+        odd = np.zeros(nc, dtype=np.int64)
+        we = np.zeros(nc, dtype=np.float64) if w is not None else None
+        wo = np.zeros(nc, dtype=np.float64) if w is not None else None
+        wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        st = _load().or_count_4pcf(self._h, _ptr(wa), _ptr(even), _ptr(odd), _ptr(we), _ptr(wo),
+                                   self.nthreads)
+        if st != 0:
+            raise ValueError(f"oracle 4pCF failed ({st})")
+        return (even, odd, we, wo) if w is not None else (even, odd)
+
+    def pairs(self, w=None):
+        p = np.zeros(self.nb, dtype=np.uint64)
+        wp = np.zeros(self.nb, dtype=np.float64)
+        wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        st = _load().or_pairs(self._h, _ptr(wa), _ptr(p), _ptr(wp))
+        if st != 0:
+            raise ValueError("oracle pairs failed")
+        return (p, wp) if w is not None else p
+
+    def disconnected(self, w=None, rr=None):
+        """(pairs u64[nb], xi f64[nb], zeta_disc f64[n_orbits])."""
+        no = num_configs(4, self.nb)
+        p = np.zeros(self.nb, dtype=np.uint64)
+        xi = np.zeros(self.nb, dtype=np.float64)
+        z = np.zeros(no, dtype=np.float64)
+        wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        rra = None if rr is None else np.ascontiguousarray(rr, dtype=np.float64)
+        st = _load().or_disconnected(self._h, _ptr(wa), _ptr(rra), _ptr(p), _ptr(xi), _ptr(z))
+        if st != 0:
+            raise ValueError(f"oracle disconnected failed ({st})")
+        return p, xi, z

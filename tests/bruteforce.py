@@ -1,0 +1,177 @@
+"""Brute-force reference for tiny inputs, used to pin the oracle.
+
+Everything here is written from the definitions with Python integers and
+itertools, independently of ``oracle/`` and of the CUDA library: all pairs
+for the graph, all triples for triangles, networkx clique enumeration for
+tetrahedra, all 24 vertex relabellings for the 4-point configuration, and
+exact Python-integer determinants for the parity volume.
+"""
+from __future__ import annotations
+
+import itertools
+from fractions import Fraction
+
+import numpy as np
+
+
+def displacements(X: np.ndarray, box_u: int) -> np.ndarray:
+    """(N, N, 3) int64 minimum-image displacements X_j - X_i."""
+    X = X.astype(np.int64)
+    d = X[None, :, :] - X[:, None, :]
+    if box_u > 0:
+        d = np.where(2 * d >= box_u, d - box_u, d)
+        d = np.where(2 * d < -box_u, d + box_u, d)
+    return d
+
+
+def bin_matrix(X: np.ndarray, box_u: int, edges_u) -> np.ndarray:
+    """(N, N) int matrix: bin of the pair, or -1 when the pair is not an edge."""
+    d = displacements(X, box_u)
+    D2 = (d * d).sum(axis=2)
+    e2 = np.asarray(edges_u, dtype=np.int64) ** 2
+    nb = len(e2) - 1
+    B = np.full(D2.shape, -1, dtype=np.int64)
+    for b in range(nb):
+        B[(D2 >= e2[b]) & (D2 < e2[b + 1])] = b
+    np.fill_diagonal(B, -1)
+    return B
+
+
+def configs3(nb: int):
+    reps = [t for t in itertools.product(range(nb), repeat=3) if t[0] <= t[1] <= t[2]]
+    return {t: k for k, t in enumerate(sorted(reps))}
+
+
+SLOTS = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+PERMS = list(itertools.permutations(range(4)))
+
+
+def perm_sign(p) -> int:
+    inv = sum(1 for a in range(4) for b in range(a + 1, 4) if p[a] > p[b])
+    return -1 if inv % 2 else 1
+
+
+def canonical4(bins_of_pair):
+    """Smallest relabelled tuple and one relabelling reaching it.
+
+    ``bins_of_pair(a, b)`` gives the bin of the edge between vertices a, b of
+    the input labelling; relabelling p puts old vertex p[k] at new label k.
+    """
+    best, bestp = None, None
+    for p in PERMS:
+        t = tuple(bins_of_pair(p[a], p[b]) for a, b in SLOTS)
+        if best is None or t < best:
+            best, bestp = t, p
+    return best, bestp
+
+
+def configs4(nb: int):
+    """Orbit representatives in lexicographic order -> (rank, chiral)."""
+    reps = set()
+    for t in itertools.product(range(nb), repeat=6):
+        def f(a, b, t=t):
+            a, b = min(a, b), max(a, b)
+            return t[SLOTS.index((a, b))]
+        reps.add(canonical4(f)[0])
+    out = {}
+    for k, r in enumerate(sorted(reps)):
+        def f(a, b, r=r):
+            a, b = min(a, b), max(a, b)
+            return r[SLOTS.index((a, b))]
+        chiral = all(perm_sign(p) > 0 for p in PERMS
+                     if tuple(f(p[a], p[b]) for a, b in SLOTS) == r)
+        out[r] = (k, chiral)
+    return out
+
+
+def det3(u, v, w) -> int:
+    return (u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+            u[2] * (v[0] * w[1] - v[1] * w[0]))
+
+
+def count3(X, box_u, edges_u, w=None):
+    nb = len(edges_u) - 1
+    B = bin_matrix(X, box_u, edges_u)
+    conf = configs3(nb)
+    counts = np.zeros(len(conf), dtype=np.uint64)
+    wsum = [Fraction(0)] * len(conf)
+    n = X.shape[0]
+    for i, j, k in itertools.combinations(range(n), 3):
+        if B[i, j] < 0 or B[i, k] < 0 or B[j, k] < 0:
+            continue
+        c = conf[tuple(sorted((int(B[i, j]), int(B[i, k]), int(B[j, k]))))]
+        counts[c] += 1
+        if w is not None:
+            wsum[c] += Fraction(float(w[i])) * Fraction(float(w[j])) * Fraction(float(w[k]))
+    if w is None:
+        return counts
+    return counts, np.array([float(x) for x in wsum])
+
+
+def count4(X, box_u, edges_u, w=None):
+    """Even/odd 4-point counts via networkx 4-cliques."""
+    import networkx as nx
+    nb = len(edges_u) - 1
+    B = bin_matrix(X, box_u, edges_u)
+    d = displacements(X, box_u)
+    conf = configs4(nb)
+    G = nx.Graph()
+    G.add_nodes_from(range(X.shape[0]))
+    ii, jj = np.nonzero(np.triu(B >= 0, 1))
+    G.add_edges_from(zip(ii.tolist(), jj.tolist()))
+    even = np.zeros(len(conf), dtype=np.uint64)
+    odd = np.zeros(len(conf), dtype=np.int64)
+    weven = [Fraction(0)] * len(conf)
+    wodd = [Fraction(0)] * len(conf)
+    for cl in nx.enumerate_all_cliques(G):
+        if len(cl) < 4:
+            continue
+        if len(cl) > 4:
+            break
+        v = list(cl)
+        rep, p = canonical4(lambda a, b: int(B[v[a], v[b]]))
+        k, chiral = conf[rep]
+        even[k] += 1
+        wt = Fraction(1)
+        if w is not None:
+            for x in v:
+                wt *= Fraction(float(w[x]))
+            weven[k] += wt
+        if chiral:
+            u = [v[p[t]] for t in range(4)]
+            vecs = [[int(d[u[0], u[t], a]) for a in range(3)] for t in (1, 2, 3)]
+            V = det3(*vecs)
+            if V != 0:
+                s = 1 if V > 0 else -1
+                odd[k] += s
+                wodd[k] += s * wt
+    if w is None:
+        return even, odd
+    return even, odd, np.array([float(x) for x in weven]), np.array([float(x) for x in wodd])
+
+
+def pairs(X, box_u, edges_u, w=None):
+    nb = len(edges_u) - 1
+    B = bin_matrix(X, box_u, edges_u)
+    out = np.zeros(nb, dtype=np.uint64)
+    wout = [Fraction(0)] * nb
+    n = X.shape[0]
+    for i in range(n):
+        for j in range(i + 1, n):
+            if B[i, j] >= 0:
+                out[B[i, j]] += 1
+                if w is not None:
+                    wout[B[i, j]] += Fraction(float(w[i])) * Fraction(float(w[j]))
+    if w is None:
+        return out
+    return out, np.array([float(x) for x in wout])
+
+
+def rows(X, box_u, edges_u):
+    """Sorted neighbour rows as a list of (ids, bins)."""
+    B = bin_matrix(X, box_u, edges_u)
+    out = []
+    for i in range(X.shape[0]):
+        j = np.nonzero(B[i] >= 0)[0]
+        out.append((j.astype(np.int64), B[i, j].astype(np.int64)))
+    return out
