@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Throughput benchmark: binned triangle counts per second on GB300.
+
+Workload (default): 1,000,000 Neyman-Scott points (parents uniform,
+Poisson(10) children, Gaussian sigma 2 h^-1Mpc) plus 3,000,000 uniform
+randoms in a periodic box L = 1000 h^-1Mpc, FP32 weights U(0.5, 1.5),
+rmax = 40 h^-1Mpc in 20 linear bins; DDD and RRR 3pCF, unweighted u64
+counts and exact weighted sums. One step = for both catalogues: lattice
+quantisation, device graph build, triangle counting (one pass that
+produces the counts and the weighted sums). Positions and weights are
+resident in HBM when the timed region starts; the graphs (about 5 GB for
+the randoms) are larger than L2, so no flush is needed between steps.
+
+Under torchrun every rank processes its own independent realisation
+(seeds offset by rank): weak scaling, no collective on the data path.
+
+--impl reference times the CPU oracle (the plain restatement of the
+paper's definitions) on a bounded hub sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import catalogs  # noqa: E402
+
+WORKLOAD = "ns1M_L1000_r40_nb20"
+METRIC = "binned triplets/s (DDD+RRR 3pCF, counts + exact weighted sums)"
+UNIT = "triplets/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-4pcf", action="store_true",
+                    help="skip the secondary 4pCF + parity measurement")
+    ap.add_argument("--profile", choices=["count3", "count4", "pairs"], default=None,
+                    help="run one small case of one kernel for an ncu capture (no JSON)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the counting kernel from the committed ncu summary."""
+    p = os.path.join(ROOT, "profiles", "count3_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if f[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload(rank):
+    spec = catalogs.WORKLOADS[WORKLOAD]
+    off = 1000 * rank
+    d = catalogs.draw(WORKLOAD, seed=spec["seed"] + off)
+    w_d = catalogs.uniform_weights(spec["n"], seed=spec["weight_seed"] + off)
+    pos_r = catalogs.uniform(spec["randoms"], spec["box"], seed=spec["random_seed"] + off)
+    w_r = catalogs.uniform_weights(spec["randoms"], seed=spec["weight_seed"] + 7 + off)
+    return d, [(d["pos"], w_d), (pos_r, w_r)]
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle arm
+
+
+def oracle_rate(cats, box_u, edges, seconds, nthreads):
+    """Triangles/s of the oracle's 3pCF over the first hubs of the data
+    catalogue (query time only; its graph build is not timed)."""
+    import oracle
+    X = oracle.quantize(cats[0][0], box_u, True)
+    g = oracle.Graph(X, box_u, edges, nthreads=nthreads)
+    w = cats[0][1]
+    k = 2000
+    t0 = time.perf_counter()
+    c, _ = g.count_3pcf(w, hub_lo=0, hub_hi=k)
+    dt = time.perf_counter() - t0
+    k = int(min(X.shape[0], max(k, k * seconds / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    c, _ = g.count_3pcf(w, hub_lo=0, hub_hi=k)
+    dt = time.perf_counter() - t0
+    return float(c.sum()) / dt, k, dt, g
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    spec, cats = load_workload(0)
+    box_u, edges = spec["box_u"], spec["edges_u"]
+    nthreads = oracle.default_threads()
+    X = oracle.quantize(cats[0][0], box_u, True)
+    g = oracle.Graph(X, box_u, edges, nthreads=nthreads)
+    w = cats[0][1]
+    # size one step to about budget / (steps + warmup) seconds
+    per_step = max(2.0, 150.0 / (args.steps + args.warmup))
+    k = 2000
+    t0 = time.perf_counter()
+    g.count_3pcf(w, hub_lo=0, hub_hi=k)
+    dt = time.perf_counter() - t0
+    k = int(min(X.shape[0], max(k, k * per_step / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        g.count_3pcf(w, hub_lo=0, hub_hi=k)
+    tri, t0 = 0.0, time.perf_counter()
+    for _ in range(args.steps):
+        c, _ = g.count_3pcf(w, hub_lo=0, hub_hi=k)
+        tri += float(c.sum())
+    dt = time.perf_counter() - t0
+    value = tri / dt
+    sample = (f"oracle 3pCF (counts + exact weighted sums) over hubs [0, {k}) of the "
+              f"1e6-point Neyman-Scott data catalogue, query time only")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "hubs_per_step": k},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+
+
+def run_ours(args):
+    import ctypes
+
+    import torch
+
+    import paper_2607_06604_gb300 as gs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec, cats = load_workload(rank)
+    box_u, edges = spec["box_u"], spec["edges_u"]
+    stream = torch.cuda.current_stream()
+    dev = [(torch.from_numpy(p).cuda(), torch.from_numpy(w).cuda()) for p, w in cats]
+    xyz = [torch.empty((p.shape[0], 3), dtype=torch.int32, device="cuda") for p, _ in dev]
+    nconf = gs.gs_num_configs(3, len(edges) - 1)
+    counts = [torch.empty(nconf, dtype=torch.uint64, device="cuda") for _ in dev]
+    wsums = [torch.empty(nconf, dtype=torch.float64, device="cuda") for _ in dev]
+    kms = ctypes.c_double(0.0)
+    kernel_ms = []
+
+    def step(record=False):
+        for c, (pos, w) in enumerate(dev):
+            gs.gs_quantize(pos, box_u, True, out=xyz[c], stream=stream)
+            g = gs.gs_build_graph(xyz[c], box_u, edges, stream=stream)
+            gs.gs_count_3pcf(g, w, counts=counts[c], wsum=wsums[c], stream=stream, kernel_ms=kms)
+            if record and c == 1:
+                kernel_ms.append(kms.value)
+            g.close()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tri_step = float(sum(int(c.sum().item()) for c in counts))
+    # statistics of the randoms' graph for the roofline (outside the timed region)
+    g = gs.gs_build_graph(gs.gs_quantize(dev[1][0], box_u, True), box_u, edges)
+    info = gs.gs_graph_info(g)
+    g.close()
+
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        launches0 = gs.gs_kernel_launches()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        launches = gs.gs_kernel_launches() - launches0
+    barrier()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    tri_t = torch.tensor([tri_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tri_t, op=torch.distributed.ReduceOp.SUM)
+    ms = float(ms_t.item())
+    total_tri = float(tri_t.item()) * args.steps
+    value = total_tri / (ms / 1e3)
+
+    # end to end through the public API: pinned host inputs copied in, the
+    # counts and weighted sums read back, every step
+    pinned = [(torch.from_numpy(p).pin_memory(), torch.from_numpy(w).pin_memory()) for p, w in cats]
+    host_out = [(torch.empty(nconf, dtype=torch.uint64).pin_memory(),
+                 torch.empty(nconf, dtype=torch.float64).pin_memory()) for _ in cats]
+    h2d = sum(p.numel() * p.element_size() + w.numel() * w.element_size() for p, w in pinned)
+    d2h = sum(c.numel() * c.element_size() + s.numel() * s.element_size() for c, s in host_out)
+
+    def step_e2e():
+        for c, (pos_h, w_h) in enumerate(pinned):
+            pos = pos_h.to("cuda", non_blocking=True)
+            w = w_h.to("cuda", non_blocking=True)
+            x = gs.gs_quantize(pos, box_u, True, stream=stream)
+            g = gs.gs_build_graph(x, box_u, edges, stream=stream)
+            gs.gs_count_3pcf(g, w, counts=counts[c], wsum=wsums[c], stream=stream)
+            host_out[c][0].copy_(counts[c], non_blocking=True)
+            host_out[c][1].copy_(wsums[c], non_blocking=True)
+            g.close()
+        torch.cuda.synchronize()
+
+    step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    barrier()
+    e_s = time.perf_counter() - e0
+    e_t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = total_tri / float(e_t.item())
+
+    # roofline of the dominant kernel (RRR counting)
+    peak, peak_kind = measured_peaks()
+    bpe = info["bytes_per_edge"]
+    alg_bytes = bpe * (info["edges"] + info["walk_words"])
+    k_ms = float(np.mean(kernel_ms)) if kernel_ms else float("nan")
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    traffic = recorded_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "k_count3 (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+            "triangles_per_launch": float(counts[1].sum().item())}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        nthreads = oracle.default_threads()
+        rate, k, dt, _ = oracle_rate(cats, box_u, edges, args.cpu_seconds, nthreads)
+        cpu = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"oracle 3pCF (counts + exact weighted sums) over hubs [0, {k}) of the "
+                         f"1e6-point data catalogue, query time only ({dt:.1f} s)"}
+    clocks = clk.summary()
+    quad = None
+    if not args.no_4pcf:
+        quad = measure_4pcf(gs, torch)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_data": spec["n"], "n_randoms": spec["randoms"],
+                       "box": spec["box"], "rmax": spec["rmax"], "nb": spec["nb"],
+                       "weights": "fp32 U(0.5,1.5), exact fixed-point sums",
+                       "parallelism": f"independent realisation per rank x{world}",
+                       "l2": "inputs larger than L2 (randoms' graph "
+                             f"{info['edge_slots'] * bpe / 1e9:.1f} GB)"},
+            "triangles_per_step": tri_step,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "clocks": clocks, "quadruplets": quad,
+            "graph_randoms": {k2: info[k2] for k2 in ("edges", "max_degree", "probe_words",
+                                                      "walk_words", "edge_slots")}}
+    print(json.dumps(line), flush=True)
+
+
+def measure_4pcf(gs, torch, runs=2):
+    """Quadruplets/s of the parity 4pCF on 2e5 Neyman-Scott points (L=400,
+    rmax 30 in 8 bins), plus the pair sweep and disconnected term."""
+    spec = catalogs.draw("ns200k_L400_r30_nb8")
+    box_u, edges = spec["box_u"], spec["edges_u"]
+    pos = torch.from_numpy(spec["pos"]).cuda()
+    g = gs.gs_build_graph(gs.gs_quantize(pos, box_u, True), box_u, edges)
+    like = pos
+    gs.gs_count_4pcf_parity(g, like=like)
+    import ctypes
+    km = ctypes.c_double(0.0)
+    ms = []
+    for _ in range(runs):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        even, odd = gs.gs_count_4pcf_parity(g, like=like, kernel_ms=km)
+        t1.record()
+        torch.cuda.synchronize()
+        ms.append(t0.elapsed_time(t1))
+    tet = float(even.sum().item())
+    pk = ctypes.c_double(0.0)
+    gs.gs_disconnected_4pcf(g, like=like, kernel_ms=pk)
+    info = gs.gs_graph_info(g)
+    g.close()
+    best = min(ms)
+    return {"workload": "ns200k_L400_r30_nb8", "metric": "binned quadruplets/s (4pCF even+odd)",
+            "value": tet / (best / 1e3), "unit": "quadruplets/s", "tetrahedra": tet,
+            "call_ms": best, "kernel_ms": km.value, "pair_sweep_ms": pk.value,
+            "pair_sweep_gbs": info["edge_slots"] * 4 / (pk.value / 1e3) / 1e9 if pk.value else None,
+            "odd_abs_sum": float(odd.abs().sum().item())}
+
+
+def run_profile(args):
+    """One small case per kernel, sized above L2 but a few GB at most."""
+    import torch
+
+    import paper_2607_06604_gb300 as gs
+    torch.cuda.set_device(0)
+    if args.profile in ("count3", "pairs"):
+        # 1e6 uniform points at the randoms' density (3e-3 per (h^-1 Mpc)^3),
+        # rmax 40 in 20 bins: a 1.6 GB graph
+        L = 693.0
+        box_u = int(L * 1024)
+        pos = torch.from_numpy(catalogs.uniform(1_000_000, L, seed=5)).cuda()
+        edges = catalogs.bin_edges_u(0.0, 40.0, 20)
+        g = gs.gs_build_graph(gs.gs_quantize(pos, box_u, True), box_u, edges)
+        for _ in range(2):
+            if args.profile == "count3":
+                gs.gs_count_3pcf(g, like=pos)
+            else:
+                gs.gs_disconnected_4pcf(g, like=pos, zeta=False)
+    else:
+        # 1e5 Neyman-Scott points at the 4pCF workload's density (L=317)
+        L = 317.0
+        box_u = int(L * 1024)
+        pos = torch.from_numpy(catalogs.neyman_scott(100_000, L, seed=6, sigma=2.0)).cuda()
+        edges = catalogs.bin_edges_u(0.0, 30.0, 8)
+        g = gs.gs_build_graph(gs.gs_quantize(pos, box_u, True), box_u, edges)
+        for _ in range(2):
+            gs.gs_count_4pcf_parity(g, like=pos)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "info": gs.gs_graph_info(g)}))
+
+
+def main():
+    args = parse()
+    if args.profile:
+        run_profile(args)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    if int(os.environ.get("WORLD_SIZE", 1)) > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * gramsci_gb300.h - C ABI of the GB300 (sm_103a) query engine for binned
+ * 3-point and 4-point correlation tuple counts over a fixed-radius graph,
+ * after GRAMSCI v2 (Sabiu, "Fast Graph-based Higher-Order Clustering
+ * Statistics on the GPU").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Coordinates are int32 lattice coordinates in units of 1/1024 h^-1 Mpc
+ * (gs_quantize makes them from float positions). A periodic box has side
+ * box_u > 0 lattice units and displacements use the minimum image
+ * (2d >= box_u: d -= box_u; 2d < -box_u: d += box_u); box_u == 0 selects an
+ * open box. Radial bins are given by nb+1 strictly increasing integer edges
+ * E_0 < ... < E_nb (lattice units); a pair with squared distance D2 is an
+ * edge iff E_0^2 <= D2 < E_nb^2 and its bin is the largest b with
+ * E_b^2 <= D2 (Sec. 2.1).
+ *
+ * Pointers: every array argument may be host or device memory (the library
+ * asks the CUDA runtime which). Inputs are owned by the caller and never
+ * retained after the call returns. Outputs are allocated by the caller,
+ * overwritten (not accumulated) and complete when the call returns: every
+ * call synchronises options->stream before returning.
+ *
+ * Streams: all device work of a call is queued on options->stream (a
+ * cudaStream_t; NULL = the legacy default stream). options may be NULL,
+ * which means all fields zero.
+ *
+ * Output order: configuration index = rank of the configuration's canonical
+ * representative in lexicographic order. 3-point: sorted bin triples
+ * (r1 <= r2 <= r3), C(nb+2, 3) of them (Sec. 5.1). 4-point: S4 orbits of the
+ * edge-bin tuple (b01, b02, b03, b12, b13, b23) represented by their
+ * lexicographically smallest member (Sec. 5.2); gs_config_bins lists them.
+ *
+ * Status: 0 on success, else one of the negative GS_E* codes below; on
+ * error the outputs are unspecified, nothing stays allocated and the
+ * library remains usable. gs_strerror gives a message.
+ */
+#ifndef GRAMSCI_GB300_H
+#define GRAMSCI_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GS_OK = 0,
+  GS_EINVAL = -1,       /* NULL where an array is required, nb < 1, bad flag */
+  GS_ERANGE = -2,       /* value outside the supported range (see each call) */
+  GS_ENOMEM = -3,       /* allocation failed, or the device budget is too small */
+  GS_ECUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+  GS_ETIMEOUT = -5,     /* a bounded device-side wait expired */
+  GS_EUNSUPPORTED = -6  /* weights whose exact weighted sums would not fit */
+};
+
+/* Opaque device-resident neighbour graph, owned by the library. */
+typedef struct gs_graph gs_graph;
+
+typedef struct {
+  /* Device-memory cap for the graph's edge storage in bytes; 0 = no cap.
+   * A graph above the cap keeps its edges in pinned host memory and every
+   * query streams row windows through device buffers (out-of-core mode). */
+  uint64_t device_budget_bytes;
+  /* > 0 forces that many row windows (out-of-core mode even when the
+   * graph fits); 0 = automatic. */
+  int32_t force_windows;
+  /* Kernel variant: 0 = automatic. 1 = exercise the long-row code paths
+   * on any input (gs_count_3pcf stages hub rows in 64-word segments;
+   * gs_count_4pcf* keeps every hub's workspace in global memory). Results
+   * are identical; variant 1 is slower and meant for testing. */
+  int32_t variant;
+  /* cudaStream_t for all device work; NULL = legacy default stream. */
+  void* stream;
+  /* Reserved, must be 0. */
+  uint32_t flags;
+  /* NULL, or receives the device time in milliseconds of the call's main
+   * kernel launches (the counting kernels of gs_count_*, the two row passes
+   * of gs_build_graph, the pair sweep of gs_disconnected_4pcf), measured
+   * with CUDA events on options->stream. */
+  double* kernel_ms;
+} gs_options;
+
+/* Graph statistics (host struct filled by gs_graph_info). */
+typedef struct {
+  int64_t n;               /* points */
+  int32_t nb;              /* radial bins */
+  int32_t max_degree;      /* largest |N+(i)| */
+  int64_t edges;           /* unordered edges = sum_i |N+(i)| */
+  int64_t edge_slots;      /* stored edge words including row padding */
+  int64_t probe_words;     /* sum over edges (i,j), i<j, of |N+(j)| */
+  int64_t bytes_per_edge;  /* bytes of one stored edge word (4 or 8) */
+  int64_t device_bytes;    /* device bytes held by the graph */
+  int32_t windows;         /* row windows (1 = fully resident) */
+  int32_t cells;           /* cells per axis of the build grid (x) */
+  int64_t walk_words;      /* sum over edges (i,j), i<j, of the words of N+(j)
+                              up to the largest id of N+(i): what a merge-walk
+                              of the spoke row reads before the hub row is
+                              exhausted (Sec. 3.1) */
+} gs_graph_stats;
+
+/*
+ * gs_quantize - positions in h^-1 Mpc to lattice coordinates (the input
+ * step of Sec. 2.1). X = floor(1024 x) per axis; periodic (periodic != 0)
+ * wraps X modulo box_u, otherwise X must lie in [0, box_u).
+ *   pos  float64 [n][3] (row-major), xyz int32 [n][3] out.
+ * Errors: GS_EINVAL (NULL, n < 0, box_u <= 0), GS_ERANGE (an open-box
+ * coordinate outside [0, box_u), or box_u >= 2^31).
+ */
+int gs_quantize(const double* pos, int64_t n, int64_t box_u, int periodic, int32_t* xyz,
+                const gs_options* options);
+
+/*
+ * gs_build_graph - radius-search graph of Sec. 2.1 (Eq. adjacency) built on
+ * the device with a cell list. The library relabels points in cell order;
+ * outputs of every query are invariant under relabelling.
+ *   xyz      int32 [n][3] lattice coordinates (periodic: in [0, box_u);
+ *            open: in [0, 2^30)).
+ *   box_u    periodic box side in lattice units, 0 = open box.
+ *   edges_u  int64 [nb+1] strictly increasing bin edges, E_0 >= 0.
+ *   out      receives the new graph; release it with gs_free_graph.
+ * Errors: GS_EINVAL (NULL, n < 0, nb < 1), GS_ERANGE (nb > 254, edges not
+ * strictly increasing, E_nb >= 2^19, 4 E_nb >= box_u for a periodic box,
+ * n >= 2^31, a coordinate out of range), GS_ENOMEM.
+ */
+int gs_build_graph(const int32_t* xyz, int64_t n, int64_t box_u, const int64_t* edges_u, int nb,
+                   const gs_options* options, gs_graph** out);
+
+/* gs_graph_info - fill *stats (host pointer). */
+int gs_graph_info(const gs_graph* g, gs_graph_stats* stats);
+
+/*
+ * gs_graph_export - copy the oriented CSR out, in the graph's own labels.
+ *   ptr  int64 [n+1]: row i holds N+(i) = {j > i adjacent to i} in
+ *        nbr[ptr[i] .. ptr[i]+deg(i)) in ascending order (rows are padded,
+ *        so ptr[i+1]-ptr[i] may exceed deg(i)).
+ *   deg  int32 [n], nbr int32 [edge_slots], bin uint8 [edge_slots],
+ *   perm int32 [n]: perm[k] = caller index of internal label k.
+ * Any output may be NULL. Host or device pointers.
+ */
+int gs_graph_export(const gs_graph* g, int64_t* ptr, int32_t* deg, int32_t* nbr, uint8_t* bin,
+                    int32_t* perm);
+
+/*
+ * gs_count_3pcf - binned triangle counts (Sec. 2.2) found with a
+ * hub-and-spoke intersection of sorted rows (Sec. 3.1).
+ *   w       NULL (unweighted) or float32 [n] weights in caller order.
+ *   counts  uint64 [C(nb+2,3)] triangle counts per configuration.
+ *   wsum    NULL or float64 [C(nb+2,3)]: sum of w_i w_j w_k per
+ *           configuration, accumulated exactly and rounded once.
+ * Errors: GS_EINVAL, GS_EUNSUPPORTED (weights not finite, or spanning so
+ * many binades that the exact sums would not fit), GS_ETIMEOUT, GS_ECUDA.
+ */
+int gs_count_3pcf(const gs_graph* g, const float* w, uint64_t* counts, double* wsum,
+                  const gs_options* options);
+
+/*
+ * gs_count_4pcf - binned tetrahedron counts (Sec. 2.2, Sec. 3.1.1):
+ * tetrahedra whose six pairs are all edges, one count per S4 orbit.
+ *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact).
+ * Errors: as gs_count_3pcf; GS_ERANGE when nb > 16.
+ */
+int gs_count_4pcf(const gs_graph* g, const float* w, uint64_t* counts, double* wsum,
+                  const gs_options* options);
+
+/*
+ * gs_count_4pcf_parity - parity-decomposed 4pCF (Sec. 3.2, Eq. volume).
+ * For each tetrahedron V = (r_01 x r_02) . r_03 is evaluated exactly in
+ * integers in the vertex order that maps it onto its orbit representative.
+ *   even  uint64 [n_orbits]: every tetrahedron (equals gs_count_4pcf).
+ *   odd   int64 [n_orbits]: sum of sign(V) over tetrahedra with V != 0 in
+ *         chiral orbits (orbits whose representative no odd permutation
+ *         fixes); zero for achiral orbits. Degenerate tetrahedra (V == 0)
+ *         add nothing to odd.
+ *   weven, wodd: NULL or float64 [n_orbits], the same with weights.
+ * Errors: as gs_count_4pcf.
+ */
+int gs_count_4pcf_parity(const gs_graph* g, const float* w, uint64_t* even, int64_t* odd,
+                         double* weven, double* wodd, const gs_options* options);
+
+/*
+ * gs_disconnected_4pcf - internal 2pCF and disconnected 4pCF on the same
+ * graph (Sec. 3.3, Eq. disc), one sweep over the edges.
+ *   w          NULL or float32 [n] weights (pair sums use w_i w_j, exact).
+ *   rr         NULL: analytic random pairs of a periodic box,
+ *              RR[b] = P (4 pi / 3)(E_{b+1}^3 - E_b^3) / box_u^3 with
+ *              P = n(n-1)/2, or ((sum w)^2 - sum w^2)/2 with weights;
+ *              else float64 [nb] random pair counts supplied by the caller.
+ *   pairs      NULL or uint64 [nb] unordered edge counts per bin.
+ *   xi         NULL or float64 [nb]: pair sum / RR - 1.
+ *   zeta_disc  NULL or float64 [n_orbits]: xi(r01) xi(r23) + xi(r02) xi(r13)
+ *              + xi(r03) xi(r12) on each orbit representative, FP64, left to
+ *              right, no fused multiply-add.
+ * Errors: GS_EINVAL (rr NULL for an open box), GS_ERANGE (zeta_disc with
+ * nb > 16), GS_EUNSUPPORTED, GS_ECUDA.
+ */
+int gs_disconnected_4pcf(const gs_graph* g, const float* w, const double* rr, uint64_t* pairs,
+                         double* xi, double* zeta_disc, const gs_options* options);
+
+/* gs_num_configs - number of configurations: npoint 3 -> C(nb+2,3);
+ * npoint 4 -> (nb^6 + 9 nb^4 + 14 nb^2) / 24 (Sec. 5.1, Sec. 5.2).
+ * Errors: GS_EINVAL (npoint not 3 or 4, nb < 1), GS_ERANGE (npoint 4 with
+ * nb > 16, npoint 3 with nb > 254). */
+int gs_num_configs(int npoint, int nb, int64_t* n);
+
+/* gs_config_bins - canonical representative of configuration idx: 3 bins
+ * (npoint 3) or 6 bins in slot order (01,02,03,12,13,23) (npoint 4);
+ * *chiral (may be NULL) is 1 for chiral 4-point orbits, else 0. Host
+ * pointers. Errors: as gs_num_configs, GS_ERANGE for idx out of range. */
+int gs_config_bins(int npoint, int nb, int64_t idx, uint8_t* bins, int* chiral);
+
+/* gs_kernel_launches - number of CUDA kernels this library has launched in
+ * this process (all devices, all threads). */
+uint64_t gs_kernel_launches(void);
+
+/* gs_free_graph - release a graph (NULL is ignored). */
+void gs_free_graph(gs_graph* g);
+
+/* gs_strerror - static message for a status code. */
+const char* gs_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAMSCI_GB300_H */

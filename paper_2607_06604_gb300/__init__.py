@@ -1,0 +1,274 @@
+"""Python binding of libgramsci_gb300 (GB300 / sm_103a query engine).
+
+Binned 3pCF / 4pCF tuple counts over a fixed-radius neighbour graph after
+GRAMSCI v2: graph of Sec. 2.1, hub-and-spoke enumeration of Sec. 2.2 /
+Sec. 3.1, parity channels of Sec. 3.2, disconnected term of Sec. 3.3.
+
+Every function below has the name of the C entry point it marshals
+arguments for (include/gramsci_gb300.h); all arithmetic runs in the CUDA
+library. Array arguments may be NumPy arrays (host) or torch tensors (host
+or CUDA); outputs are allocated like the first array input unless given.
+A missing or unbuildable library raises at import time: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
+    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_4pcf",
+    "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_num_configs", "gs_config_bins",
+    "gs_free_graph", "gs_strerror", "gs_kernel_launches", "lib_path",
+]
+
+
+class GSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {gs_strerror(status)} ({status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("force_windows", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("kernel_ms", ctypes.POINTER(ctypes.c_double))]
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("max_degree", ctypes.c_int32),
+                ("edges", ctypes.c_int64), ("edge_slots", ctypes.c_int64),
+                ("probe_words", ctypes.c_int64), ("bytes_per_edge", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("windows", ctypes.c_int32),
+                ("cells", ctypes.c_int32), ("walk_words", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    # (re)build in-tree when missing or older than its sources; raises when
+    # nvcc is missing or the build fails
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    P, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    OP = ctypes.POINTER(Options)
+    sig = {
+        "gs_quantize": ([P, i64, i64, ci, P, OP], ci),
+        "gs_build_graph": ([P, i64, i64, P, ci, OP, ctypes.POINTER(P)], ci),
+        "gs_graph_info": ([P, ctypes.POINTER(GraphStats)], ci),
+        "gs_graph_export": ([P, P, P, P, P, P], ci),
+        "gs_count_3pcf": ([P, P, P, P, OP], ci),
+        "gs_count_4pcf": ([P, P, P, P, OP], ci),
+        "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
+        "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
+        "gs_num_configs": ([ci, ci, ctypes.POINTER(i64)], ci),
+        "gs_config_bins": ([ci, ci, i64, P, ctypes.POINTER(ci)], ci),
+        "gs_free_graph": ([P], None),
+        "gs_strerror": ([ci], ctypes.c_char_p),
+        "gs_kernel_launches": ([], ctypes.c_uint64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib, path
+
+
+_lib, lib_path = _load()
+
+
+def gs_kernel_launches() -> int:
+    return int(_lib.gs_kernel_launches())
+
+
+def gs_strerror(status: int) -> str:
+    return _lib.gs_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise GSError(status, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _empty_like_input(ref, shape, np_dtype):
+    """Output on the same side (host NumPy / torch device) as ``ref``."""
+    if ref is not None and _is_torch(ref):
+        import torch
+        tdt = {np.uint64: torch.uint64, np.int64: torch.int64, np.float64: torch.float64,
+               np.int32: torch.int32, np.uint8: torch.uint8}[np_dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=np_dtype)
+
+
+def _options(stream=None, budget=0, force_windows=0, variant=0, kernel_ms=None):
+    o = Options()
+    if kernel_ms is not None:  # a ctypes.c_double receiving the kernel time
+        o.kernel_ms = ctypes.pointer(kernel_ms)
+    o.device_budget_bytes = int(budget)
+    o.force_windows = int(force_windows)
+    o.variant = int(variant)
+    if stream is not None:
+        o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    return o
+
+
+def gs_num_configs(npoint: int, nb: int) -> int:
+    n = ctypes.c_int64(0)
+    _check(_lib.gs_num_configs(int(npoint), int(nb), ctypes.byref(n)), "gs_num_configs")
+    return n.value
+
+
+def gs_config_bins(npoint: int, nb: int, idx: int):
+    bins = np.zeros(6, dtype=np.uint8)
+    chiral = ctypes.c_int(0)
+    _check(_lib.gs_config_bins(int(npoint), int(nb), int(idx), _ptr(bins), ctypes.byref(chiral)),
+           "gs_config_bins")
+    k = 3 if npoint == 3 else 6
+    return tuple(int(b) for b in bins[:k]), bool(chiral.value)
+
+
+def gs_quantize(pos, box_u: int, periodic: bool, out=None, **opts):
+    """Float positions (h^-1 Mpc) -> int32 lattice coordinates."""
+    n = int(pos.shape[0])
+    if out is None:
+        out = _empty_like_input(pos, (n, 3), np.int32)
+    o = _options(**opts)
+    _check(_lib.gs_quantize(_ptr(pos), n, int(box_u), int(bool(periodic)), _ptr(out),
+                            ctypes.byref(o)), "gs_quantize")
+    return out
+
+
+class Graph:
+    """Owning handle of a device-resident gs_graph."""
+
+    def __init__(self, handle, nb: int, n: int):
+        self._h = handle
+        self.nb = nb
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.gs_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gs_build_graph(xyz, box_u: int, edges_u, **opts) -> Graph:
+    n = int(xyz.shape[0])
+    edges = np.ascontiguousarray(np.asarray(edges_u, dtype=np.int64))
+    nb = len(edges) - 1
+    h = ctypes.c_void_p()
+    o = _options(**opts)
+    _check(_lib.gs_build_graph(_ptr(xyz), n, int(box_u), _ptr(edges), nb, ctypes.byref(o),
+                               ctypes.byref(h)), "gs_build_graph")
+    return Graph(h, nb, n)
+
+
+def gs_free_graph(g: Graph):
+    g.close()
+
+
+def gs_graph_info(g: Graph) -> dict:
+    s = GraphStats()
+    _check(_lib.gs_graph_info(g.handle, ctypes.byref(s)), "gs_graph_info")
+    return s.as_dict()
+
+
+def gs_graph_export(g: Graph):
+    """Oriented CSR in internal labels: (ptr, deg, nbr, bin, perm) NumPy arrays."""
+    info = gs_graph_info(g)
+    n, slots = info["n"], info["edge_slots"]
+    ptr = np.empty(n + 1, np.int64)
+    deg = np.empty(n, np.int32)
+    nbr = np.empty(slots, np.int32)
+    b = np.empty(slots, np.uint8)
+    perm = np.empty(n, np.int32)
+    _check(_lib.gs_graph_export(g.handle, _ptr(ptr), _ptr(deg), _ptr(nbr), _ptr(b), _ptr(perm)),
+           "gs_graph_export")
+    return ptr, deg, nbr, b, perm
+
+
+def gs_count_3pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
+    """Triangle counts per configuration (and exact weighted sums when w is given)."""
+    nc = gs_num_configs(3, g.nb)
+    ref = like if like is not None else w
+    if counts is None:
+        counts = _empty_like_input(ref, (nc,), np.uint64)
+    if w is not None and wsum is None:
+        wsum = _empty_like_input(ref, (nc,), np.float64)
+    o = _options(**opts)
+    _check(_lib.gs_count_3pcf(g.handle, _ptr(w), _ptr(counts), _ptr(wsum), ctypes.byref(o)),
+           "gs_count_3pcf")
+    return (counts, wsum) if w is not None else counts
+
+
+def gs_count_4pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
+    nc = gs_num_configs(4, g.nb)
+    ref = like if like is not None else w
+    if counts is None:
+        counts = _empty_like_input(ref, (nc,), np.uint64)
+    if w is not None and wsum is None:
+        wsum = _empty_like_input(ref, (nc,), np.float64)
+    o = _options(**opts)
+    _check(_lib.gs_count_4pcf(g.handle, _ptr(w), _ptr(counts), _ptr(wsum), ctypes.byref(o)),
+           "gs_count_4pcf")
+    return (counts, wsum) if w is not None else counts
+
+
+def gs_count_4pcf_parity(g: Graph, w=None, like=None, **opts):
+    """(even u64, odd i64) or, with weights, (even, odd, weven, wodd)."""
+    nc = gs_num_configs(4, g.nb)
+    ref = like if like is not None else w
+    even = _empty_like_input(ref, (nc,), np.uint64)
+    odd = _empty_like_input(ref, (nc,), np.int64)
+    we = _empty_like_input(ref, (nc,), np.float64) if w is not None else None
+    wo = _empty_like_input(ref, (nc,), np.float64) if w is not None else None
+    o = _options(**opts)
+    _check(_lib.gs_count_4pcf_parity(g.handle, _ptr(w), _ptr(even), _ptr(odd), _ptr(we), _ptr(wo),
+                                     ctypes.byref(o)), "gs_count_4pcf_parity")
+    return (even, odd, we, wo) if w is not None else (even, odd)
+
+
+def gs_disconnected_4pcf(g: Graph, w=None, rr=None, like=None, zeta=True, **opts):
+    """(pairs u64[nb], xi f64[nb], zeta_disc f64[n_orbits] or None)."""
+    ref = like if like is not None else w
+    pairs = _empty_like_input(ref, (g.nb,), np.uint64)
+    xi = _empty_like_input(ref, (g.nb,), np.float64)
+    z = _empty_like_input(ref, (gs_num_configs(4, g.nb),), np.float64) if zeta else None
+    if rr is not None and not _is_torch(rr):
+        rr = np.ascontiguousarray(rr, dtype=np.float64)
+    o = _options(**opts)
+    _check(_lib.gs_disconnected_4pcf(g.handle, _ptr(w), _ptr(rr), _ptr(pairs), _ptr(xi), _ptr(z),
+                                     ctypes.byref(o)), "gs_disconnected_4pcf")
+    return pairs, xi, z

@@ -1,0 +1,501 @@
+// Binned tetrahedron counts (Sec. 2.2) and the parity-decomposed channels
+// (Sec. 3.2, Eq. volume), GB300 layout.
+//
+// A tetrahedron i < a < b < c is counted at its smallest vertex i. For hub i
+// with m = |N+(i)| neighbours (local indices 0..m-1 in id order), a
+// persistent CTA
+//   1. stages N+(i) in shared memory with a bulk (TMA) copy, with the
+//      minimum-image displacement of every neighbour from i;
+//   2. builds a hash id -> local index and, with one warp per spoke a,
+//      streams N+(j_a) and sets bit c of row a of an m x m bit matrix for
+//      every c > a adjacent to a (the paper's per-hub connectivity matrix,
+//      Sec. 3.5.2, as bits);
+//   3. for every triangle (a, b), b a bit of row a, takes the common bits
+//      of rows a and b above b: each is a tetrahedron (i, a, b, c). This is
+//      the three-way walk of Eq. (threeway) done 32 candidates per word.
+// The six bins come from the staged row (hub edges) and from the staged
+// displacements (the other three edges, recomputed exactly in integers).
+// A table maps the raw bin tuple to its S4 orbit, the parity of one
+// relabelling onto the orbit representative and the orbit's chirality; the
+// signed volume is det[d_a, d_b, d_c] in 64-bit integers, multiplied by
+// that parity. Counts use per-CTA shared-memory histograms flushed with
+// 64-bit atomics. Hubs with more than kMaxSmemRow neighbours run in a
+// second launch whose per-hub workspace lives in global scratch.
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxSmemRow = 512;
+
+struct Args {
+  const int64_t* __restrict__ ptr;
+  const int32_t* __restrict__ deg;
+  const uint32_t* __restrict__ adj;  // row i at adj + (ptr[i] - adj_off)
+  int64_t adj_off;
+  int64_t hub_begin, hub_end;
+  const int4* __restrict__ xyzp;
+  const int64_t* __restrict__ e2g;
+  const uint32_t* __restrict__ lut;
+  int64_t n, box;
+  int nb, n_orbits;
+  int row_lo, row_hi;  // this launch handles hubs with row_lo <= deg <= row_hi
+  int mcap;            // workspace capacity (words)
+  unsigned long long* even;
+  unsigned long long* odd;
+  unsigned long long* weven;  // [n_orbits][3] 192-bit
+  unsigned long long* wodd;
+  const int64_t* __restrict__ W;
+  unsigned long long* hub_counter;
+  int* err;
+  unsigned char* gscratch;  // BIG: per-CTA workspace
+  size_t gscratch_stride;
+};
+
+__device__ inline int64_t mi(int64_t d, int64_t box) {
+  if (box) {
+    if (2 * d >= box) d -= box;
+    else if (2 * d < -box) d += box;
+  }
+  return d;
+}
+
+__device__ inline int bin_of(int64_t D2, const int64_t* e2, int nb) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (e2[mid] <= D2) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ inline int64_t d2(const int4& p, const int4& q) {
+  const int64_t x = (int64_t)q.x - p.x, y = (int64_t)q.y - p.y, z = (int64_t)q.z - p.z;
+  return x * x + y * y + z * z;
+}
+
+struct Workspace {
+  uint32_t* row;      // staged N+(i) words (m4)
+  int4* disp;         // displacement of each neighbour from the hub
+  unsigned long long* table;  // hash: (id << 32) | local index, empty = ~0
+  uint32_t* bits;     // m x W bit matrix
+  uint16_t* queue;    // per-warp (a, b) queue: kWarps x 64
+};
+
+template <bool PARITY, bool WEIGHTED, bool BIG>
+__global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ int64_t s_hub;
+  __shared__ int s_flush;
+  __shared__ unsigned long long s_pending;
+  __shared__ int64_t e2[kMaxBins4 + 1];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = a.nb;
+  unsigned* h_even = reinterpret_cast<unsigned*>(smem);
+  int* h_odd = reinterpret_cast<int*>(h_even + a.n_orbits);
+  unsigned char* ws_base = smem + (size_t)a.n_orbits * 4 * (PARITY ? 2 : 1);
+  ws_base = reinterpret_cast<unsigned char*>(((uintptr_t)ws_base + 15) & ~(uintptr_t)15);
+  if (BIG) ws_base = a.gscratch + (size_t)blockIdx.x * a.gscratch_stride;
+  const int mcap = a.mcap;
+  const int Wcap = (mcap + 31) / 32;
+  int tcap_bits = 5;
+  while ((1 << tcap_bits) < 2 * mcap) ++tcap_bits;
+  Workspace w;
+  {
+    unsigned char* p = ws_base;
+    w.row = reinterpret_cast<uint32_t*>(p);
+    p += (size_t)pad_row(mcap) * 4;
+    w.disp = reinterpret_cast<int4*>(p);
+    p += (size_t)mcap * 16;
+    w.table = reinterpret_cast<unsigned long long*>(p);
+    p += (size_t)(1 << tcap_bits) * 8;
+    w.bits = reinterpret_cast<uint32_t*>(p);
+    p += (size_t)mcap * Wcap * 4;
+    w.queue = reinterpret_cast<uint16_t*>(p);
+  }
+  uint16_t* q = w.queue + warp * 64;
+
+  for (int k = tid; k < a.n_orbits; k += kThreads) {
+    h_even[k] = 0;
+    if (PARITY) h_odd[k] = 0;
+  }
+  for (int b = tid; b <= nb; b += kThreads) e2[b] = a.e2g[b];
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    s_pending = 0;
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  auto flush = [&]() {
+    for (int k = tid; k < a.n_orbits; k += kThreads) {
+      const unsigned c = h_even[k];
+      if (c) {
+        atomicAdd(a.even + k, (unsigned long long)c);
+        h_even[k] = 0;
+      }
+      if (PARITY) {
+        const int o = h_odd[k];
+        if (o) {
+          atomicAdd(a.odd + k, (unsigned long long)(long long)o);
+          h_odd[k] = 0;
+        }
+      }
+    }
+  };
+
+  for (;;) {
+    if (tid == 0) {
+      int64_t i;
+      int d;
+      do {  // skip hubs this launch does not handle
+        i = a.hub_begin + (int64_t)atomicAdd(a.hub_counter, 1ull);
+        d = (i < a.hub_end) ? a.deg[i] : 0;
+      } while (i < a.hub_end && (d < 3 || d < a.row_lo || d > a.row_hi));
+      s_hub = i;
+      s_flush = 0;
+      if (i < a.hub_end) {
+        const unsigned long long m = (unsigned long long)d;
+        const unsigned long long need = m * (m - 1) * (m - 2) / 6;
+        if (!BIG && s_pending + need > 0x7FFFFFFFull) {
+          s_flush = 1;
+          s_pending = need;
+        } else {
+          s_pending += need;
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t i = s_hub;
+    if (i >= a.hub_end) break;
+    if (s_flush) {
+      flush();
+      __syncthreads();
+    }
+    const int m = a.deg[i];
+    const int W = (m + 31) / 32;
+    const uint32_t* grow = a.adj + (a.ptr[i] - a.adj_off);
+    const uint32_t* row = w.row;
+    if (!BIG) {
+      if (tid == 0) bulk_load(w.row, grow, (uint32_t)pad_row(m) * 4u, &bar);
+    } else {
+      row = grow;
+    }
+    int tbits = 5;
+    while ((1 << tbits) < 2 * m) ++tbits;
+    const int T = 1 << tbits, shift = 32 - tbits;
+    for (int k = tid; k < T; k += kThreads) w.table[k] = ~0ull;
+    for (int k = tid; k < m * W; k += kThreads) w.bits[k] = 0u;
+    if (!BIG) {
+      const bool ok = mbar_wait(&bar, phase, kWaitLimit);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(a.err, kErrTimeout);
+        return;
+      }
+    } else {
+      __syncthreads();
+    }
+    const int4 P = a.xyzp[i];
+    for (int k = tid; k < m; k += kThreads) {
+      const uint32_t wd = row[k];
+      const uint32_t id = edge_id(wd);
+      const int4 Q = a.xyzp[id];
+      w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
+                            (int)mi((int64_t)Q.z - P.z, a.box), 0);
+      uint32_t h = (id * kHashMul) >> shift;
+      const unsigned long long ent = ((unsigned long long)id << 32) | (unsigned)k;
+      while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
+    }
+    __syncthreads();
+    // bit matrix: row a gets bit c for every c > a adjacent to j_a
+    const uint32_t hub_hi = edge_id(row[m - 1]);
+    for (int sa = warp; sa < m - 1; sa += kWarps) {
+      const uint32_t j = edge_id(row[sa]);
+      const uint32_t* rj = a.adj + (a.ptr[j] - a.adj_off);
+      const int dj4 = (int)pad_row(a.deg[j]);
+      for (int t0 = 0; t0 < dj4; t0 += 128) {
+        const int t = t0 + lane * 4;
+        const uint4 v = (t < dj4) ? ldg_nc_v4(rj + t)
+                                  : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const uint32_t key = edge_id(vv[qq]);
+          if (key > hub_hi) continue;
+          uint32_t h = (key * kHashMul) >> shift;
+          for (;;) {
+            const unsigned long long e = w.table[h];
+            if (e == ~0ull) break;
+            if ((uint32_t)(e >> 32) == key) {
+              const int c = (int)(e & 0xffffffffu);
+              atomicOr(w.bits + sa * W + (c >> 5), 1u << (c & 31));
+              break;
+            }
+            h = (h + 1) & (T - 1);
+          }
+        }
+        const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+        if (edge_id(last) > hub_hi) break;
+      }
+    }
+    __syncthreads();
+    // tetrahedra: warp per row a; (a, b) pairs queued 32 at a time
+    const int64_t Wi = WEIGHTED ? a.W[i] : 0;
+    for (int sa = warp; sa < m - 2; sa += kWarps) {
+      const uint32_t wa = row[sa];
+      const int b01 = (int)edge_bin(wa);
+      const int4 da = w.disp[sa];
+      const int64_t Wia = WEIGHTED ? Wi * a.W[edge_id(wa)] : 0;
+      int qn = 0;
+      const uint32_t* bra = w.bits + sa * W;
+      for (int wd = sa >> 5; wd <= W; ++wd) {
+        uint32_t x = 0;
+        if (wd < W) x = bra[wd];
+        const bool drain = (wd == W);
+        const bool set = (x >> lane) & 1u;
+        const unsigned m_set = __ballot_sync(0xffffffffu, set);
+        if (set) q[qn + __popc(m_set & ((1u << lane) - 1u))] = (uint16_t)(wd * 32 + lane);
+        qn += __popc(m_set);
+        __syncwarp();
+        while (qn >= 32 || (drain && qn > 0)) {
+          const bool active = lane < qn;
+          const int sb = active ? q[lane] : 0;
+          __syncwarp();
+          if (active) {
+            const uint32_t wb = row[sb];
+            const int b02 = (int)edge_bin(wb);
+            const int4 db = w.disp[sb];
+            const int b12 = bin_of(d2(da, db), e2, nb);
+            const uint32_t* lrow = a.lut + (size_t)((b01 * nb + b02) * nb + b12) * nb * nb * nb;
+            const uint32_t* brb = w.bits + sb * W;
+            const int64_t Wb = WEIGHTED ? a.W[edge_id(wb)] : 0;
+            for (int wc = sb >> 5; wc < W; ++wc) {
+              uint32_t x2 = bra[wc] & brb[wc];
+              if (wc == (sb >> 5)) x2 &= ~((2u << (sb & 31)) - 1u);
+              while (x2) {
+                const int sc = wc * 32 + __ffs(x2) - 1;
+                x2 &= x2 - 1u;
+                const uint32_t wcw = row[sc];
+                const int4 dc = w.disp[sc];
+                const int b03 = (int)edge_bin(wcw);
+                const int b13 = bin_of(d2(da, dc), e2, nb);
+                const int b23 = bin_of(d2(db, dc), e2, nb);
+                const uint32_t ent = lrow[(b03 * nb + b13) * nb + b23];
+                const int orbit = (int)(ent & 0x3FFFFFFFu);
+                if (BIG) atomicAdd(a.even + orbit, 1ull);
+                else atomicAdd(h_even + orbit, 1u);
+                long long plo = 0, phi = 0;
+                // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
+                if (WEIGHTED) mul_i128(Wia, Wb * a.W[edge_id(wcw)], &plo, &phi);
+                if (WEIGHTED)
+                  atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
+                if (PARITY && (ent >> 31)) {
+                  const int64_t V =
+                      (int64_t)da.x * ((int64_t)db.y * dc.z - (int64_t)db.z * dc.y) -
+                      (int64_t)da.y * ((int64_t)db.x * dc.z - (int64_t)db.z * dc.x) +
+                      (int64_t)da.z * ((int64_t)db.x * dc.y - (int64_t)db.y * dc.x);
+                  if (V != 0) {
+                    int sgn = V > 0 ? 1 : -1;
+                    if ((ent >> 30) & 1u) sgn = -sgn;
+                    if (BIG) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
+                    else atomicAdd(h_odd + orbit, sgn);
+                    if (WEIGHTED) {
+                      unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
+                      if (sgn < 0) {  // negate the 128-bit product
+                        lo = ~lo + 1ull;
+                        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+                      }
+                      atomic_add_i192(a.wodd + 3 * orbit, lo, hi);
+                    }
+                  }
+                }
+              }
+            }
+          }
+          if (qn >= 32) {
+            // move the overflow entries (queue holds at most 63)
+            const int rest = qn - 32;
+            uint16_t mv = 0;
+            if (lane < rest) mv = q[32 + lane];
+            __syncwarp();
+            if (lane < rest) q[lane] = mv;
+            __syncwarp();
+            qn = rest;
+          } else {
+            qn = 0;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  flush();
+}
+
+size_t workspace_bytes(int mcap) {
+  int tbits = 5;
+  while ((1 << tbits) < 2 * mcap) ++tbits;
+  const size_t Wc = (size_t)(mcap + 31) / 32;
+  return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + ((size_t)1 << tbits) * 8 +
+         (size_t)mcap * Wc * 4 + (size_t)kWarps * 64 * 2 + 64;
+}
+
+}  // namespace
+
+__global__ void k_i192_to_double(const unsigned long long* acc, int64_t n, int scale, double* out);
+__global__ void k_u64_to_double(const unsigned long long* c, int64_t n, double* out);
+__global__ void k_i64_to_double(const long long* c, int64_t n, double* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (double)c[k];
+}
+
+int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
+                  int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc) {
+  cudaStream_t s = o.stream;
+  int st = GS_OK;
+  const Conf4Tables* t = conf4_tables(g.nb, &st);
+  if (!t) return st;
+  const int no = (int)t->n_orbits;
+  const bool weighted = fw != nullptr;
+  Args a;
+  a.ptr = g.d_ptr;
+  a.deg = g.d_deg;
+  a.adj = nullptr;
+  a.adj_off = 0;
+  a.hub_begin = 0;
+  a.hub_end = g.n;
+  a.xyzp = g.d_xyzp;
+  a.e2g = g.d_edges2;
+  a.lut = t->d_lut;
+  a.n = g.n;
+  a.box = g.box_u;
+  a.nb = g.nb;
+  a.n_orbits = no;
+  a.even = reinterpret_cast<unsigned long long*>(d_even);
+  a.odd = parity ? (d_odd ? reinterpret_cast<unsigned long long*>(d_odd)
+                          : sc.alloc<unsigned long long>(no))
+                 : nullptr;
+  a.W = weighted ? fw->d_W : nullptr;
+  a.weven = weighted ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
+  a.wodd = (weighted && parity) ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
+  a.hub_counter = sc.alloc<unsigned long long>(2);
+  a.err = sc.alloc<int>(1);
+  if (!a.hub_counter || !a.err || (parity && !a.odd) || (weighted && !a.weven) ||
+      (weighted && parity && !a.wodd))
+    return GS_ENOMEM;
+  cudaMemsetAsync(a.even, 0, sizeof(uint64_t) * no, s);
+  if (parity) cudaMemsetAsync(a.odd, 0, sizeof(uint64_t) * no, s);
+  if (a.weven) cudaMemsetAsync(a.weven, 0, sizeof(unsigned long long) * 3 * no, s);
+  if (a.wodd) cudaMemsetAsync(a.wodd, 0, sizeof(unsigned long long) * 3 * no, s);
+  cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long) * 2, s);
+  cudaMemsetAsync(a.err, 0, sizeof(int), s);
+
+  int dev = 0, sms = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t hist_bytes = (size_t)no * 4 * (parity ? 2 : 1);
+  const size_t hist_aligned = (hist_bytes + 15) & ~(size_t)15;
+  // largest smem row that fits next to the histograms
+  int mcap = kMaxSmemRow;
+  while (mcap > 32 && hist_aligned + workspace_bytes(mcap) > (size_t)optin - 1024) mcap -= 32;
+  if (hist_aligned + workspace_bytes(mcap) > (size_t)optin - 1024) return GS_ERANGE;
+
+  auto pick = [&](bool big) -> void (*)(Args) {
+    if (parity) {
+      if (weighted) return big ? k_count4<true, true, true> : k_count4<true, true, false>;
+      return big ? k_count4<true, false, true> : k_count4<true, false, false>;
+    }
+    if (weighted) return big ? k_count4<false, true, true> : k_count4<false, true, false>;
+    return big ? k_count4<false, false, true> : k_count4<false, false, false>;
+  };
+  // variant 1 sends every hub to the global-workspace launch (exercises it
+  // on any input)
+  const bool force_global = (o.variant & 1) != 0;
+  void (*kern_s)(Args) = pick(false);
+  const size_t smem_s = hist_aligned + workspace_bytes(mcap);
+  cudaFuncSetAttribute(kern_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern_s, kThreads, smem_s);
+  const bool need_big = g.max_deg > mcap || (force_global && g.max_deg >= 3);
+  void (*kern_b)(Args) = pick(true);
+  const size_t smem_b = hist_aligned;
+  size_t stride_b = 0;
+  unsigned char* scratch_b = nullptr;
+  if (need_big) {
+    cudaFuncSetAttribute(kern_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+    stride_b = (workspace_bytes(g.max_deg) + 255) & ~(size_t)255;
+    scratch_b = sc.alloc<unsigned char>(stride_b * sms);
+    if (!scratch_b) return GS_ENOMEM;
+  }
+  KernelTimer timer(o.kernel_ms);
+  timer.start(s);
+  st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
+                                     int64_t h1) -> int {
+    a.adj = adj;
+    a.adj_off = off;
+    a.hub_begin = h0;
+    a.hub_end = h1;
+    cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long) * 2, s);
+    // launch 1: rows up to mcap, workspace in shared memory
+    if (!force_global) {
+      Args b = a;
+      b.row_lo = 0;
+      b.row_hi = mcap;
+      b.mcap = mcap;
+      b.gscratch = nullptr;
+      b.gscratch_stride = 0;
+      { kern_s<<<std::max(1, per_sm) * sms, kThreads, smem_s, s>>>(b); note_launch(); }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    // launch 2: longer rows, workspace in global scratch sized from the
+    // longest row of the graph
+    if (need_big) {
+      Args b = a;
+      b.row_lo = force_global ? 0 : mcap + 1;
+      b.row_hi = g.max_deg;
+      b.mcap = g.max_deg;
+      b.gscratch_stride = stride_b;
+      b.gscratch = scratch_b;
+      b.hub_counter = a.hub_counter + 1;
+      { kern_b<<<sms, kThreads, smem_b, s>>>(b); note_launch(); }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    return GS_OK;
+  });
+  if (st) return st;
+  timer.stop(s);
+  if (d_weven) {
+    if (weighted)
+      { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(a.weven, no, 4 * fw->scale, d_weven); note_launch(); }
+    else
+      { k_u64_to_double<<<(no + 255) / 256, 256, 0, s>>>(a.even, no, d_weven); note_launch(); }
+  }
+  if (d_wodd && parity) {
+    if (weighted)
+      { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(a.wodd, no, 4 * fw->scale, d_wodd); note_launch(); }
+    else
+      { k_i64_to_double<<<(no + 255) / 256, 256, 0, s>>>(reinterpret_cast<const long long*>(a.odd), no,
+                                                       d_wodd); note_launch(); }
+  }
+  int herr = 0;
+  cudaMemcpyAsync(&herr, a.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  timer.publish();
+  return herr ? GS_ETIMEOUT : GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,192 @@
+// Internal 2pCF and the disconnected 4pCF term (Sec. 3.3, Eq. disc).
+//
+// The unweighted pair histogram is one streaming pass over the packed edge
+// words (the bin is the low byte of every word; padding words carry bin
+// 0xFF and are skipped), 128-bit loads, per-CTA shared-memory counters.
+// The weighted pass walks rows (warp per hub) to pair w_i with w_j, in
+// exact fixed point. A single small kernel then forms RR, xi and
+// zeta_disc in FP64 with explicitly rounded operations (no contraction),
+// in the order the equation is written.
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+__global__ void k_i192_to_double(const unsigned long long* acc, int64_t n, int scale, double* out);
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) k_pairs_count(const uint4* __restrict__ adj4,
+                                                          int64_t n4, int nb,
+                                                          unsigned long long* pairs) {
+  __shared__ unsigned h[kMaxBins + 2];
+  for (int b = threadIdx.x; b <= kMaxBins + 1; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n4;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 v = adj4[k];
+    const uint32_t b[4] = {edge_bin(v.x), edge_bin(v.y), edge_bin(v.z), edge_bin(v.w)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (b[q] < (uint32_t)nb) atomicAdd(h + b[q], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+    if (h[b]) atomicAdd(pairs + b, (unsigned long long)h[b]);
+}
+
+// Weighted pair sums sum_{i<j} W_i W_j per bin (192-bit), and the weight
+// moments sum W_i and sum W_i^2 (for the analytic random pair count).
+__global__ void __launch_bounds__(kThreads) k_pairs_weighted(
+    const int64_t* __restrict__ ptr, const int32_t* __restrict__ deg,
+    const uint32_t* __restrict__ adj, int64_t adj_off, const int64_t* __restrict__ W,
+    int64_t h0, int64_t h1, int nb, unsigned long long* pairs, unsigned long long* wpairs,
+    unsigned long long* moments) {
+  __shared__ unsigned long long acc[2 * (kMaxBins + 1)];
+  __shared__ unsigned cnt[kMaxBins + 1];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    acc[2 * b] = acc[2 * b + 1] = 0;
+    cnt[b] = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = h0 + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < h1;
+       i += warps) {
+    const int64_t Wi = W[i];
+    const int d = deg[i];
+    const uint32_t* r = adj + (ptr[i] - adj_off);
+    for (int k = lane; k < d; k += 32) {
+      const uint32_t w = r[k];
+      const int b = (int)edge_bin(w);
+      long long lo, hi;
+      mul_i128(Wi, W[edge_id(w)], &lo, &hi);
+      atomic_add_i128(acc + 2 * b, lo, hi);
+      atomicAdd(cnt + b, 1u);
+    }
+    if (lane == 0) {
+      long long lo, hi;
+      mul_i128(Wi, Wi, &lo, &hi);
+      atomic_add_i192(moments + 3, (unsigned long long)lo, (unsigned long long)hi);
+      atomic_add_i192(moments, (unsigned long long)Wi, (unsigned long long)(Wi < 0 ? -1ll : 0ll));
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    if (acc[2 * b] | acc[2 * b + 1]) atomic_add_i192(wpairs + 3 * b, acc[2 * b], acc[2 * b + 1]);
+    if (cnt[b]) atomicAdd(pairs + b, (unsigned long long)cnt[b]);
+  }
+}
+
+__global__ void k_xi_disc(const unsigned long long* pairs, const double* wpairs_d,
+                          const double* moments_d, const double* rr, const int64_t* e2g, int nb,
+                          int64_t n, int64_t box, int weighted, double* xi_out,
+                          const uint8_t* reps, int64_t n_orbits, double* zeta) {
+  __shared__ double xi[kMaxBins + 1];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    double RR;
+    if (rr) {
+      RR = rr[b];
+    } else {
+      double P;
+      if (weighted) {
+        const double S1 = moments_d[0], S2 = moments_d[1];
+        P = __ddiv_rn(__dsub_rn(__dmul_rn(S1, S1), S2), 2.0);
+      } else {
+        P = __ddiv_rn(__dmul_rn((double)n, (double)(n - 1)), 2.0);
+      }
+      // edges from their squares (exact: the squares are perfect squares)
+      const int64_t e0 = (int64_t)llrint(sqrt((double)e2g[b]));
+      const int64_t e1 = (int64_t)llrint(sqrt((double)e2g[b + 1]));
+      const double dv = (double)(e1 * e1 * e1 - e0 * e0 * e0);
+      const double four_pi_3 = __ddiv_rn(__dmul_rn(4.0, 3.14159265358979323846), 3.0);
+      const double vb = __dmul_rn(four_pi_3, dv);
+      const double L = (double)box;
+      const double vbox = __dmul_rn(__dmul_rn(L, L), L);
+      RR = __ddiv_rn(__dmul_rn(P, vb), vbox);
+    }
+    const double num = weighted ? wpairs_d[b] : (double)pairs[b];
+    const double x = __dsub_rn(__ddiv_rn(num, RR), 1.0);
+    xi[b] = x;
+    if (xi_out) xi_out[b] = x;
+  }
+  __syncthreads();
+  if (!zeta) return;
+  for (int64_t o = threadIdx.x; o < n_orbits; o += blockDim.x) {
+    const uint8_t* r = reps + 6 * o;  // slots 01 02 03 12 13 23
+    const double t1 = __dmul_rn(xi[r[0]], xi[r[5]]);
+    const double t2 = __dmul_rn(xi[r[1]], xi[r[4]]);
+    const double t3 = __dmul_rn(xi[r[2]], xi[r[3]]);
+    zeta[o] = __dadd_rn(__dadd_rn(t1, t2), t3);
+  }
+}
+
+}  // namespace
+
+int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint64_t* d_pairs,
+                      double* d_xi, double* d_zeta, const Opts& o, Scratch& sc) {
+  cudaStream_t s = o.stream;
+  const int nb = g.nb;
+  int st = GS_OK;
+  const Conf4Tables* t = nullptr;
+  if (d_zeta) {
+    t = conf4_tables(nb, &st);
+    if (!t) return st;
+  }
+  unsigned long long* pairs = d_pairs ? reinterpret_cast<unsigned long long*>(d_pairs)
+                                      : sc.alloc<unsigned long long>(nb);
+  if (!pairs) return GS_ENOMEM;
+  cudaMemsetAsync(pairs, 0, sizeof(uint64_t) * nb, s);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double* wp_d = nullptr;
+  double* mom_d = nullptr;
+  KernelTimer timer(o.kernel_ms);
+  if (fw) {
+    unsigned long long* wacc = sc.alloc<unsigned long long>(3 * (size_t)nb + 6);
+    wp_d = sc.alloc<double>(nb + 2);
+    if (!wacc || !wp_d) return GS_ENOMEM;
+    cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * (3 * nb + 6), s);
+    timer.start(s);
+    if (g.n)
+      st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
+                                         int64_t h1) -> int {
+        { k_pairs_weighted<<<sms * 8, kThreads, 0, s>>>(g.d_ptr, g.d_deg, adj, off, fw->d_W, h0,
+                                                      h1, nb, pairs, wacc, wacc + 3 * nb); note_launch(); }
+        return cuda_status(cudaGetLastError());
+      });
+    timer.stop(s);
+    if (st) return st;
+    { k_i192_to_double<<<1, 256, 0, s>>>(wacc, nb, 2 * fw->scale, wp_d); note_launch(); }
+    { k_i192_to_double<<<1, 32, 0, s>>>(wacc + 3 * nb, 1, fw->scale, wp_d + nb); note_launch(); }
+    { k_i192_to_double<<<1, 32, 0, s>>>(wacc + 3 * nb + 3, 1, 2 * fw->scale, wp_d + nb + 1); note_launch(); }
+    mom_d = wp_d + nb;
+  } else if (g.slots) {
+    timer.start(s);
+    // the own rows of a window are its first ptr[h1] - ptr[h0] words
+    st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
+                                       int64_t h1) -> int {
+      const int64_t words = g.h_ptr[h1] - g.h_ptr[h0];
+      if (words)
+        { k_pairs_count<<<sms * 8, kThreads, 0, s>>>(reinterpret_cast<const uint4*>(adj), words / 4, nb,
+                                                   pairs); note_launch(); }
+      return cuda_status(cudaGetLastError());
+    });
+    timer.stop(s);
+    if (st) return st;
+  }
+  if (d_xi || d_zeta) {
+    { k_xi_disc<<<1, 1024, 0, s>>>(pairs, wp_d, mom_d, d_rr, g.d_edges2, nb, g.n, g.box_u, fw ? 1 : 0,
+                                 d_xi, t ? t->d_reps : nullptr, t ? t->n_orbits : 0, d_zeta); note_launch(); }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  timer.publish();
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace gs

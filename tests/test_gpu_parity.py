@@ -1,0 +1,376 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Unweighted counts, pair counts and lattice coordinates must match bit for
+bit; weighted sums, xi and zeta_disc within 1e-12 relative (both sides sum
+exactly and round once, so the only differences come from the final
+rounding and from FP64 evaluation order of RR).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import catalogs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2607_06604_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rand_lattice(n, box_u, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, box_u, size=(n, 3)).astype(np.int32)
+
+
+def clump(n, centre, spread, box_u, seed):
+    rng = np.random.default_rng(seed)
+    X = np.asarray(centre) + rng.integers(-spread, spread + 1, size=(n, 3))
+    return np.mod(X, box_u).astype(np.int32)
+
+
+def edge_set_from_gpu(gs, g):
+    ptr, deg, nbr, b, perm = gs.gs_graph_export(g)
+    rows = np.repeat(np.arange(len(deg)), deg)
+    cols = np.concatenate([nbr[ptr[i]:ptr[i] + deg[i]] for i in range(len(deg))]) \
+        if len(deg) else np.zeros(0, np.int64)
+    bins = np.concatenate([b[ptr[i]:ptr[i] + deg[i]] for i in range(len(deg))]) \
+        if len(deg) else np.zeros(0, np.uint8)
+    a, c = perm[rows].astype(np.int64), perm[cols].astype(np.int64)
+    lo, hi = np.minimum(a, c), np.maximum(a, c)
+    key = (lo << 40) | (hi << 8) | bins.astype(np.int64)
+    return np.sort(key), deg, ptr, nbr
+
+
+def edge_set_from_oracle(og):
+    ptr, nbr, b = og.export()
+    rows = np.repeat(np.arange(og.n), np.diff(ptr))
+    keep = nbr > rows
+    key = (rows[keep].astype(np.int64) << 40) | (nbr[keep].astype(np.int64) << 8) | \
+        b[keep].astype(np.int64)
+    return np.sort(key)
+
+
+# ----------------------------------------------------------------------------
+# a1 quantisation
+
+
+def test_quantize_bit_exact(gs, torch_mod):
+    rng = np.random.default_rng(1)
+    L = 250.0
+    box_u = int(L * 1024)
+    pos = rng.uniform(-L, 2 * L, size=(100_000, 3))
+    pos[:10] = [[0.0, 0.0, 0.0], [L, L, L], [-1e-12, 1e-12, L - 1e-9], [1 / 1024, 2 / 1024, 3 / 1024],
+                [L / 2, -L / 2, 1.5 * L], [-0.0, 0.5, 0.25], [1e-300, 7.0, 9.0],
+                [249.99999999999997, 0.1, 0.2], [-250.0, -500.0, 500.0], [3.0, 3.0, 3.0]]
+    ref = oracle.quantize(pos, box_u, True)
+    assert np.array_equal(gs.gs_quantize(pos, box_u, True), ref)
+    got = gs.gs_quantize(dev(torch_mod, pos), box_u, True)
+    assert np.array_equal(got.cpu().numpy(), ref)
+    inside = rng.uniform(0, L, size=(1000, 3))
+    assert np.array_equal(gs.gs_quantize(inside, box_u, False), oracle.quantize(inside, box_u, False))
+    with pytest.raises(gs.GSError) as e:
+        gs.gs_quantize(pos, box_u, False)
+    assert e.value.status == -2
+
+
+# ----------------------------------------------------------------------------
+# a2 graph
+
+
+def adversarial(box_u, edges_u):
+    pts = [[100, 100, 100], [100, 100, 100], [0, 0, 0], [box_u // 2, 0, 0],
+           [box_u - 1, box_u - 1, box_u - 1]]
+    base = np.array([box_u // 3, box_u // 5, box_u // 7])
+    for e in edges_u:
+        pts.append((base + [int(e), 0, 0]).tolist())
+        pts.append((base + [0, int(e) - 1, 0]).tolist())
+        pts.append((base + [0, 0, int(e) + 1]).tolist())
+    return np.mod(np.array(pts, dtype=np.int64), box_u).astype(np.int32)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_graph_edges_bit_exact(gs, periodic):
+    box_u = 120_000
+    edges = np.array([0, 2000, 3500, 5000, 6500, 8000], dtype=np.int64)
+    X = np.concatenate([rand_lattice(20_000, box_u, 3), clump(3000, [50_000] * 3, 6000, box_u, 4),
+                        adversarial(box_u, edges)])
+    bu = box_u if periodic else 0
+    g = gs.gs_build_graph(X, bu, edges)
+    got, deg, ptr, nbr = edge_set_from_gpu(gs, g)
+    og = oracle.Graph(X, bu, edges)
+    ref = edge_set_from_oracle(og)
+    assert np.array_equal(got, ref)
+    # rows sorted ascending, only ids above the hub, padding to 16 bytes
+    assert np.all(ptr % 4 == 0)
+    for i in range(0, len(deg), 97):
+        r = nbr[ptr[i]:ptr[i] + deg[i]]
+        assert np.all(np.diff(r) > 0) and (len(r) == 0 or r[0] > i)
+    info = gs.gs_graph_info(g)
+    assert info["edges"] == len(ref) and info["max_degree"] == deg.max()
+
+
+# ----------------------------------------------------------------------------
+# a3 triangles
+
+
+def run3(gs, torch, X, box_u, edges, w=None):
+    g = gs.gs_build_graph(dev(torch, X), box_u, edges)
+    if w is None:
+        return gs.gs_count_3pcf(g, like=dev(torch, np.zeros(1))).cpu().numpy()
+    c, ws = gs.gs_count_3pcf(g, dev(torch, w))
+    return c.cpu().numpy(), ws.cpu().numpy()
+
+
+def test_3pcf_uniform20k_full_size(gs, torch_mod):
+    """20,000 uniform points, L=200, rmax 20 in 10 bins: every bin bit-exact."""
+    s = catalogs.draw("uniform20k_L200_r20_nb10")
+    X = oracle.quantize(s["pos"], s["box_u"], True)
+    og = oracle.Graph(X, s["box_u"], s["edges_u"])
+    ref = og.count_3pcf()
+    got = run3(gs, torch_mod, X, s["box_u"], s["edges_u"])
+    assert ref.sum() > 10_000_000
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("periodic,seed", [(True, 11), (False, 12)])
+def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
+    L = 150.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(30_000, L, seed=seed, sigma=2.0, periodic=periodic)
+    w = catalogs.uniform_weights(pos.shape[0], seed=seed + 1)
+    X = oracle.quantize(pos, box_u, periodic)
+    edges = catalogs.bin_edges_u(0.0, 12.0, 8)
+    bu = box_u if periodic else 0
+    og = oracle.Graph(X, bu, edges)
+    rc, rw = og.count_3pcf(w)
+    gc, gw = run3(gs, torch_mod, X, bu, edges, w)
+    assert np.array_equal(gc, rc)
+    np.testing.assert_allclose(gw, rw, rtol=RTOL, atol=0)
+    # unweighted call on the same graph agrees with the weighted call's counts
+    assert np.array_equal(run3(gs, torch_mod, X, bu, edges), rc)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
+def test_3pcf_tiny_and_empty(gs, torch_mod, n):
+    box_u = 100_000
+    edges = np.array([0, 5000, 10000], dtype=np.int64)
+    X = clump(n, [500, 500, 500], 3000, box_u, n) if n else np.zeros((0, 3), np.int32)
+    ref = oracle.Graph(X, box_u, edges).count_3pcf()
+    assert np.array_equal(run3(gs, torch_mod, X, box_u, edges), ref)
+
+
+def test_3pcf_coincident_points(gs, torch_mod):
+    """50 points on one lattice site: C(50,3) triangles in configuration (0,0,0)."""
+    X = np.full((50, 3), 777, dtype=np.int32)
+    edges = np.array([0, 100, 200], dtype=np.int64)
+    got = run3(gs, torch_mod, X, 100_000, edges)
+    assert got[0] == math.comb(50, 3) and got.sum() == got[0]
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_3pcf_long_rows_segmented(gs, torch_mod, periodic):
+    """variant 1 stages hub rows in 64-word segments, so rows of ~70-200
+    neighbours run through the multi-segment path (binary-searched spoke
+    starts, spokes read from global memory)."""
+    L = 120.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(20_000, L, seed=24, sigma=2.0, periodic=periodic)
+    X = oracle.quantize(pos, box_u, periodic)
+    edges = catalogs.bin_edges_u(0.0, 14.0, 7)
+    bu = box_u if periodic else 0
+    w = catalogs.uniform_weights(X.shape[0], seed=23)
+    og = oracle.Graph(X, bu, edges)
+    ptr, _, _ = og.export()
+    assert np.diff(ptr).max() > 2 * 64
+    rc, rw = og.count_3pcf(w)
+    g = gs.gs_build_graph(dev(torch_mod, X), bu, edges)
+    gc, gw = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1)
+    assert np.array_equal(gc.cpu().numpy(), rc)
+    np.testing.assert_allclose(gw.cpu().numpy(), rw, rtol=RTOL)
+
+
+def test_3pcf_host_and_device_pointers(gs, torch_mod):
+    box_u = 60_000
+    X = rand_lattice(5000, box_u, 31)
+    edges = np.array([0, 3000, 6000], dtype=np.int64)
+    ref = oracle.Graph(X, box_u, edges).count_3pcf()
+    g_host = gs.gs_build_graph(X, box_u, edges)
+    assert np.array_equal(gs.gs_count_3pcf(g_host), ref)  # host in, host out
+    out = torch_mod.zeros(len(ref), dtype=torch_mod.uint64, device="cuda")
+    gs.gs_count_3pcf(g_host, counts=out)  # device out
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+# ----------------------------------------------------------------------------
+# a4 / a5 tetrahedra and parity
+
+
+def run4(gs, torch, X, box_u, edges, w=None):
+    g = gs.gs_build_graph(dev(torch, X), box_u, edges)
+    like = dev(torch, np.zeros(1))
+    if w is None:
+        e, o = gs.gs_count_4pcf_parity(g, like=like)
+        c = gs.gs_count_4pcf(g, like=like)
+        assert np.array_equal(c.cpu().numpy(), e.cpu().numpy())
+        return e.cpu().numpy(), o.cpu().numpy()
+    e, o, we, wo = gs.gs_count_4pcf_parity(g, dev(torch, w))
+    return e.cpu().numpy(), o.cpu().numpy(), we.cpu().numpy(), wo.cpu().numpy()
+
+
+@pytest.mark.parametrize("periodic,nb,seed", [(True, 4, 41), (False, 6, 42), (True, 8, 43)])
+def test_4pcf_parity_clustered(gs, torch_mod, periodic, nb, seed):
+    L = 100.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(12_000, L, seed=seed, sigma=1.5, periodic=periodic)
+    X = oracle.quantize(pos, box_u, periodic)
+    edges = catalogs.bin_edges_u(0.0, 9.0, nb)
+    bu = box_u if periodic else 0
+    og = oracle.Graph(X, bu, edges)
+    re, ro = og.count_4pcf()
+    ge, go = run4(gs, torch_mod, X, bu, edges)
+    assert re.sum() > 100_000 and np.abs(ro).sum() > 0
+    assert np.array_equal(ge, re)
+    assert np.array_equal(go, ro)
+
+
+def test_4pcf_weighted(gs, torch_mod):
+    box_u = 80_000
+    X = np.concatenate([rand_lattice(4000, box_u, 51), clump(300, [40_000] * 3, 5000, box_u, 52)])
+    w = catalogs.uniform_weights(X.shape[0], seed=53)
+    edges = np.array([0, 2500, 5000, 7000], dtype=np.int64)
+    og = oracle.Graph(X, box_u, edges)
+    re, ro, rwe, rwo = og.count_4pcf(w)
+    ge, go, gwe, gwo = run4(gs, torch_mod, X, box_u, edges, w)
+    assert np.array_equal(ge, re) and np.array_equal(go, ro)
+    np.testing.assert_allclose(gwe, rwe, rtol=RTOL)
+    np.testing.assert_allclose(gwo, rwo, rtol=RTOL, atol=1e-300)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_4pcf_global_workspace(gs, torch_mod, periodic):
+    """variant 1 runs every hub in the launch whose workspace lives in global
+    memory (the path taken by rows longer than the shared-memory capacity)."""
+    L = 100.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(12_000, L, seed=63, sigma=1.5, periodic=periodic)
+    X = oracle.quantize(pos, box_u, periodic)
+    edges = catalogs.bin_edges_u(0.0, 9.0, 5)
+    bu = box_u if periodic else 0
+    og = oracle.Graph(X, bu, edges)
+    re, ro = og.count_4pcf()
+    g = gs.gs_build_graph(dev(torch_mod, X), bu, edges)
+    ge, go = gs.gs_count_4pcf_parity(g, like=dev(torch_mod, np.zeros(1)), variant=1)
+    assert np.array_equal(ge.cpu().numpy(), re) and np.array_equal(go.cpu().numpy(), ro)
+
+
+@pytest.mark.parametrize("mirrored_fraction", [0.0, 0.3, 0.5])
+def test_parity_injection_gpu(gs, torch_mod, mirrored_fraction):
+    """Sec. 4.6 injection test: odd = N_L - N_R exactly at the injected orbit."""
+    gold = json.load(open(os.path.join(GOLDEN, "injection_tetrahedron.json")))
+    edges = np.array(gold["edges_u"], dtype=np.int64)
+    n = gold["n_struct"]
+    _, lat, mirrored = catalogs.lattice_tetrahedra(np.array(gold["shape_u"]), n, mirrored_fraction,
+                                                   gold["box_u"], int(edges[-1]) + 1, seed=78)
+    ge, go = run4(gs, torch_mod, lat.astype(np.int32), gold["box_u"], edges)
+    nb = len(edges) - 1
+    k = [gs.gs_config_bins(4, nb, i)[0] for i in range(gs.gs_num_configs(4, nb))].index(tuple(gold["rep"]))
+    assert ge[k] == n and ge.sum() == n
+    assert go[k] == gold["left_sign"] * (int((~mirrored).sum()) - int(mirrored.sum()))
+
+
+# ----------------------------------------------------------------------------
+# a6 pairs, xi, zeta_disc
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_disconnected_parity(gs, torch_mod, weighted):
+    L = 120.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(25_000, L, seed=71, sigma=2.0)
+    X = oracle.quantize(pos, box_u, True)
+    w = catalogs.uniform_weights(X.shape[0], seed=72) if weighted else None
+    edges = catalogs.bin_edges_u(0.0, 10.0, 6)
+    og = oracle.Graph(X, box_u, edges)
+    rp, rxi, rz = og.disconnected(w)
+    g = gs.gs_build_graph(dev(torch_mod, X), box_u, edges)
+    p, xi, z = gs.gs_disconnected_4pcf(g, None if w is None else dev(torch_mod, w),
+                                       like=dev(torch_mod, np.zeros(1)))
+    assert np.array_equal(p.cpu().numpy(), rp)
+    np.testing.assert_allclose(xi.cpu().numpy(), rxi, rtol=RTOL, atol=RTOL)
+    np.testing.assert_allclose(z.cpu().numpy(), rz, rtol=RTOL, atol=RTOL)
+    # caller-supplied RR, open box
+    rr = np.linspace(1e4, 2e4, 6)
+    og2 = oracle.Graph(X, 0, edges)
+    rp2, rxi2, rz2 = og2.disconnected(w, rr=rr)
+    g2 = gs.gs_build_graph(X, 0, edges)
+    p2, xi2, z2 = gs.gs_disconnected_4pcf(g2, w, rr=rr)
+    assert np.array_equal(p2, rp2)
+    np.testing.assert_allclose(xi2, rxi2, rtol=RTOL, atol=RTOL)
+    np.testing.assert_allclose(z2, rz2, rtol=RTOL, atol=RTOL)
+
+
+# ----------------------------------------------------------------------------
+# Full-size workloads
+
+
+@pytest.fixture(scope="module")
+def ns1m(gs):
+    s = catalogs.draw("ns1M_L1000_r40_nb20")
+    X = oracle.quantize(s["pos"], s["box_u"], True)
+    w = catalogs.uniform_weights(X.shape[0], seed=s["weight_seed"])
+    return s, X, w
+
+
+def test_full_size_ddd_bit_exact(gs, torch_mod, ns1m):
+    """1e6 Neyman-Scott points, L=1000, rmax 40 in 20 bins: DDD against the
+    oracle on every bin, unweighted bit-exact and weighted to 1e-12."""
+    s, X, w = ns1m
+    og = oracle.Graph(X, s["box_u"], s["edges_u"])
+    rc, rw = og.count_3pcf(w)
+    gc, gw = run3(gs, torch_mod, X, s["box_u"], s["edges_u"], w)
+    assert rc.sum() > 1e9
+    assert np.array_equal(gc, rc)
+    np.testing.assert_allclose(gw, rw, rtol=RTOL)
+
+
+def test_full_size_rrr_properties(gs, torch_mod):
+    """3e6 uniform randoms, L=1000, rmax 40 in 20 bins (too large for the
+    oracle): mirror and relabelling invariance hold bit for bit, and the
+    triangle total matches the Poisson closed form C(N,3) p^2 15/32."""
+    s = catalogs.draw("ns1M_L1000_r40_nb20")
+    N = s["randoms"]
+    pos = catalogs.uniform(N, s["box"], seed=s["random_seed"])
+    box_u = s["box_u"]
+    X = oracle.quantize(pos, box_u, True)
+    c0 = run3(gs, torch_mod, X, box_u, s["edges_u"])
+    Xm = X.copy()
+    Xm[:, 0] = np.mod(-Xm[:, 0].astype(np.int64), box_u).astype(np.int32)
+    assert np.array_equal(run3(gs, torch_mod, Xm, box_u, s["edges_u"]), c0)
+    perm = np.random.default_rng(9).permutation(N)
+    assert np.array_equal(run3(gs, torch_mod, X[perm], box_u, s["edges_u"]), c0)
+    p = 4 * math.pi * float(s["edges_u"][-1]) ** 3 / 3 / float(box_u) ** 3
+    expect = math.comb(N, 3) * p * p * 15 / 32
+    sd = math.sqrt(expect) * 30  # generous: triangle counts are strongly correlated
+    assert abs(float(c0.sum()) - expect) < 5 * sd
