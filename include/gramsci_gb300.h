@@ -74,6 +74,13 @@ typedef struct {
   void* stream;
   /* Reserved, must be 0. */
   uint32_t flags;
+  /* Hub sharding for multi-GPU splits of one catalogue: with shards > 1 a
+   * query counts only the tuples whose smallest internal label lies in the
+   * shard-th of `shards` contiguous hub ranges of about equal edge count;
+   * the sum over shard = 0 .. shards-1 is the full result (integer counts
+   * and exact weighted sums add exactly). shards <= 1 counts everything. */
+  int32_t shard;
+  int32_t shards;
   /* NULL, or receives the device time in milliseconds of the call's main
    * kernel launches (the counting kernels of gs_count_*, the two row passes
    * of gs_build_graph, the pair sweep of gs_disconnected_4pcf), measured
@@ -155,6 +162,21 @@ int gs_count_3pcf(const gs_graph* g, const float* w, uint64_t* counts, double* w
                   const gs_options* options);
 
 /*
+ * gs_count_3pcf_batch - gs_count_3pcf for many catalogues in one
+ * persistent launch: the hubs of all graphs form one work queue, so small
+ * catalogues share the GPU instead of each paying a launch and a tail.
+ * Results are identical to one gs_count_3pcf call per graph.
+ *   graphs   n_graphs resident graphs (not out-of-core) with equal nb.
+ *   w        NULL (all unweighted) or n_graphs weight arrays (none NULL).
+ *   counts   n_graphs output arrays of C(nb+2,3) uint64.
+ *   wsum     NULL or n_graphs arrays (an entry may be NULL) of float64.
+ * Errors: GS_EINVAL (NULL entries, unequal nb, out-of-core graph), and as
+ * gs_count_3pcf.
+ */
+int gs_count_3pcf_batch(const gs_graph* const* graphs, int32_t n_graphs, const float* const* w,
+                        uint64_t* const* counts, double* const* wsum, const gs_options* options);
+
+/*
  * gs_count_4pcf - binned tetrahedron counts (Sec. 2.2, Sec. 3.1.1):
  * tetrahedra whose six pairs are all edges, one count per S4 orbit.
  *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact).
@@ -208,6 +230,57 @@ int gs_num_configs(int npoint, int nb, int64_t* n);
  * *chiral (may be NULL) is 1 for chiral 4-point orbits, else 0. Host
  * pointers. Errors: as gs_num_configs, GS_ERANGE for idx out of range. */
 int gs_config_bins(int npoint, int nb, int64_t idx, uint8_t* bins, int* chiral);
+
+/* ------------------------------------------------------------------------
+ * Request loop (continuous batching of catalogue queries).
+ *
+ * A server owns two host threads and two CUDA streams on the device that
+ * was current at gs_server_create. Requests are admitted in arrival order
+ * while the graphs held on the device fit in device_budget_bytes (a request
+ * that alone exceeds it runs when nothing else is held); graph builds of
+ * admitted requests overlap the counting of earlier ones; ready 3pCF
+ * requests with equal nb and weighting are counted together in one batched
+ * persistent launch (as gs_count_3pcf_batch); 4pCF requests run the parity
+ * kernel one by one. Results are identical to single calls.
+ */
+typedef struct gs_server gs_server;
+
+typedef struct {
+  uint64_t device_budget_bytes; /* graph memory admitted at once; 0 = 80% of free */
+  int32_t max_batch;            /* catalogues per batched launch; 0 = 64 */
+  int32_t reserved;             /* must be 0 */
+} gs_server_config;
+
+typedef struct {
+  const int32_t* xyz;     /* [n][3] lattice coordinates (host), copied at submit */
+  int64_t n;
+  int64_t box_u;          /* periodic side, 0 = open box */
+  const int64_t* edges_u; /* [nb+1], copied at submit */
+  int32_t nb;
+  int32_t npoint;         /* 3: gs_count_3pcf; 4: gs_count_4pcf_parity */
+  const float* w;         /* NULL or [n] weights (host), copied at submit */
+  /* Outputs: caller-owned HOST arrays that must stay valid until
+   * gs_server_wait returns for this ticket. */
+  uint64_t* counts;       /* 3pCF counts, or 4pCF even channel */
+  int64_t* odd;           /* 4pCF odd channel (required for npoint 4) */
+  double* wsum;           /* NULL, or weighted sums (3pCF) / weighted even (4pCF) */
+} gs_request;
+
+typedef struct {
+  int32_t status;   /* the request's GS_* status */
+  double t_submit;  /* seconds since gs_server_create */
+  double t_start;   /* admitted (graph build begins) */
+  double t_done;    /* results written */
+} gs_ticket_info;
+
+int gs_server_create(const gs_server_config* cfg, gs_server** out);
+/* Queue a request; *ticket identifies it. Errors: GS_EINVAL. */
+int gs_server_submit(gs_server* s, const gs_request* req, int64_t* ticket);
+/* Block until the ticket completes (timeout_s < 0: no limit); returns its
+ * status, or GS_ETIMEOUT if the wait timed out (the ticket stays valid). */
+int gs_server_wait(gs_server* s, int64_t ticket, double timeout_s, gs_ticket_info* info);
+/* Finish every queued request, stop the threads, release the server. */
+int gs_server_destroy(gs_server* s);
 
 /* gs_kernel_launches - number of CUDA kernels this library has launched in
  * this process (all devices, all threads). */

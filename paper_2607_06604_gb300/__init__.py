@@ -22,9 +22,9 @@ from . import build as _build
 
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
-    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_4pcf",
+    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_3pcf_batch", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_num_configs", "gs_config_bins",
-    "gs_free_graph", "gs_strerror", "gs_kernel_launches", "lib_path",
+    "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "lib_path",
 ]
 
 
@@ -37,7 +37,8 @@ class GSError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("force_windows", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("flags", ctypes.c_uint32), ("kernel_ms", ctypes.POINTER(ctypes.c_double))]
+                ("flags", ctypes.c_uint32), ("shard", ctypes.c_int32), ("shards", ctypes.c_int32),
+                ("kernel_ms", ctypes.POINTER(ctypes.c_double))]
 
 
 class GraphStats(ctypes.Structure):
@@ -49,6 +50,23 @@ class GraphStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("xyz", ctypes.c_void_p), ("n", ctypes.c_int64), ("box_u", ctypes.c_int64),
+                ("edges_u", ctypes.c_void_p), ("nb", ctypes.c_int32), ("npoint", ctypes.c_int32),
+                ("w", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("odd", ctypes.c_void_p),
+                ("wsum", ctypes.c_void_p)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 def _load():
@@ -65,6 +83,7 @@ def _load():
         "gs_graph_export": ([P, P, P, P, P, P], ci),
         "gs_count_3pcf": ([P, P, P, P, OP], ci),
         "gs_count_4pcf": ([P, P, P, P, OP], ci),
+        "gs_count_3pcf_batch": ([P, ctypes.c_int32, P, P, P, OP], ci),
         "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
         "gs_num_configs": ([ci, ci, ctypes.POINTER(i64)], ci),
@@ -72,6 +91,10 @@ def _load():
         "gs_free_graph": ([P], None),
         "gs_strerror": ([ci], ctypes.c_char_p),
         "gs_kernel_launches": ([], ctypes.c_uint64),
+        "gs_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(P)], ci),
+        "gs_server_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(i64)], ci),
+        "gs_server_wait": ([P, i64, ctypes.c_double, ctypes.POINTER(TicketInfo)], ci),
+        "gs_server_destroy": ([P], ci),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -122,8 +145,11 @@ def _empty_like_input(ref, shape, np_dtype):
     return np.empty(shape, dtype=np_dtype)
 
 
-def _options(stream=None, budget=0, force_windows=0, variant=0, kernel_ms=None):
+def _options(stream=None, budget=0, force_windows=0, variant=0, kernel_ms=None, shard=0,
+             shards=0):
     o = Options()
+    o.shard = int(shard)
+    o.shards = int(shards)
     if kernel_ms is not None:  # a ctypes.c_double receiving the kernel time
         o.kernel_ms = ctypes.pointer(kernel_ms)
     o.device_budget_bytes = int(budget)
@@ -233,6 +259,24 @@ def gs_count_3pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
     return (counts, wsum) if w is not None else counts
 
 
+def gs_count_3pcf_batch(graphs, ws=None, like=None, **opts):
+    """One persistent launch over several graphs; returns [(counts, wsum|None)]."""
+    n = len(graphs)
+    nc = gs_num_configs(3, graphs[0].nb)
+    ref = like if like is not None else (ws[0] if ws else None)
+    counts = [_empty_like_input(ref, (nc,), np.uint64) for _ in graphs]
+    wsums = [_empty_like_input(ref, (nc,), np.float64) for _ in graphs] if ws else None
+    P = ctypes.c_void_p
+    harr = (P * n)(*[g.handle for g in graphs])
+    carr = (P * n)(*[_ptr(c) for c in counts])
+    warr = (P * n)(*[_ptr(x) for x in ws]) if ws else None
+    sarr = (P * n)(*[_ptr(x) for x in wsums]) if ws else None
+    o = _options(**opts)
+    _check(_lib.gs_count_3pcf_batch(harr, n, warr, carr, sarr, ctypes.byref(o)),
+           "gs_count_3pcf_batch")
+    return [(c, wsums[k] if ws else None) for k, c in enumerate(counts)]
+
+
 def gs_count_4pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
     nc = gs_num_configs(4, g.nb)
     ref = like if like is not None else w
@@ -272,3 +316,56 @@ def gs_disconnected_4pcf(g: Graph, w=None, rr=None, like=None, zeta=True, **opts
     _check(_lib.gs_disconnected_4pcf(g.handle, _ptr(w), _ptr(rr), _ptr(pairs), _ptr(xi), _ptr(z),
                                      ctypes.byref(o)), "gs_disconnected_4pcf")
     return pairs, xi, z
+
+
+class gs_server:
+    """Request loop (gs_server_* in the C ABI). Submitted inputs are copied;
+    output arrays are allocated here (host NumPy) and handed back by wait()."""
+
+    def __init__(self, device_budget_bytes: int = 0, max_batch: int = 0):
+        cfg = ServerConfig(int(device_budget_bytes), int(max_batch), 0)
+        self._h = ctypes.c_void_p()
+        _check(_lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "gs_server_create")
+        self._live = {}
+
+    def submit(self, xyz, box_u, edges_u, npoint=3, w=None) -> int:
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32)
+        edges = np.ascontiguousarray(edges_u, dtype=np.int64)
+        nb = len(edges) - 1
+        nc = gs_num_configs(npoint, nb)
+        counts = np.zeros(nc, np.uint64)
+        odd = np.zeros(nc, np.int64) if npoint == 4 else None
+        wsum = np.zeros(nc, np.float64) if w is not None else None
+        wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        r = Request(_ptr(xyz), xyz.shape[0], int(box_u), _ptr(edges), nb, npoint, _ptr(wa),
+                    _ptr(counts), _ptr(odd), _ptr(wsum))
+        t = ctypes.c_int64(0)
+        _check(_lib.gs_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "gs_server_submit")
+        self._live[t.value] = (counts, odd, wsum)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """(counts, odd|None, wsum|None, info dict)."""
+        info = TicketInfo()
+        st = _lib.gs_server_wait(self._h, int(ticket), float(timeout_s), ctypes.byref(info))
+        _check(st, "gs_server_wait")
+        counts, odd, wsum = self._live.pop(ticket)
+        return counts, odd, wsum, {"t_submit": info.t_submit, "t_start": info.t_start,
+                                   "t_done": info.t_done}
+
+    def close(self):
+        if self._h:
+            _lib.gs_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

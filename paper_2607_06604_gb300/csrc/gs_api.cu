@@ -19,6 +19,8 @@ Opts read_opts(const gs_options* o) {
     r.variant = o->variant;
     r.stream = static_cast<cudaStream_t>(o->stream);
     r.kernel_ms = o->kernel_ms;
+    r.shard = o->shard;
+    r.shards = o->shards;
   }
   return r;
 }
@@ -660,6 +662,51 @@ int gs_count_3pcf(const gs_graph* G, const float* w, uint64_t* counts, double* w
       st = cuda_status(cudaMemcpyAsync(counts, dc, sizeof(uint64_t) * nc, cudaMemcpyDeviceToHost, o.stream));
     if (!st && dw && dw != wsum)
       st = cuda_status(cudaMemcpyAsync(wsum, dw, sizeof(double) * nc, cudaMemcpyDeviceToHost, o.stream));
+    cudaError_t e = cudaStreamSynchronize(o.stream);
+    if (!st) st = cuda_status(e);
+  }
+  return st;
+}
+
+int gs_count_3pcf_batch(const gs_graph* const* graphs, int32_t n_graphs, const float* const* w,
+                        uint64_t* const* counts, double* const* wsum, const gs_options* options) {
+  if (!graphs || !counts || n_graphs < 1) return GS_EINVAL;
+  const int nb = graphs[0] ? graphs[0]->g.nb : 0;
+  for (int k = 0; k < n_graphs; ++k) {
+    if (!graphs[k] || !counts[k] || graphs[k]->g.nb != nb) return GS_EINVAL;
+    if (!graphs[k]->g.d_adj) return GS_EINVAL;  // out-of-core graphs are counted one by one
+    if (w && !w[k]) return GS_EINVAL;
+  }
+  const Opts o = read_opts(options);
+  const int64_t nc = num_conf3(nb);
+  int st = GS_OK;
+  {
+    Scratch sc(o.stream);
+    std::vector<FixedW> fws(w ? n_graphs : 0);
+    std::vector<const Graph*> gr(n_graphs);
+    std::vector<uint64_t*> dc(n_graphs);
+    std::vector<double*> dw(wsum ? n_graphs : 0);
+    for (int k = 0; k < n_graphs; ++k) {
+      gr[k] = &graphs[k]->g;
+      if (w) {
+        st = prepare_weights(*gr[k], w[k], &fws[k], sc, o.stream);
+        if (st) return st;
+      }
+      dc[k] = is_device_ptr(counts[k]) ? counts[k] : sc.alloc<uint64_t>(nc);
+      if (!dc[k]) return GS_ENOMEM;
+      if (wsum) {
+        dw[k] = !wsum[k] ? nullptr : (is_device_ptr(wsum[k]) ? wsum[k] : sc.alloc<double>(nc));
+        if (wsum[k] && !dw[k]) return GS_ENOMEM;
+      }
+    }
+    st = count3_batch_device(gr.data(), n_graphs, w ? fws.data() : nullptr, dc.data(),
+                             wsum ? dw.data() : nullptr, o, sc);
+    for (int k = 0; k < n_graphs && !st; ++k) {
+      if (dc[k] != counts[k])
+        st = cuda_status(cudaMemcpyAsync(counts[k], dc[k], sizeof(uint64_t) * nc, cudaMemcpyDeviceToHost, o.stream));
+      if (!st && wsum && wsum[k] && dw[k] != wsum[k])
+        st = cuda_status(cudaMemcpyAsync(wsum[k], dw[k], sizeof(double) * nc, cudaMemcpyDeviceToHost, o.stream));
+    }
     cudaError_t e = cudaStreamSynchronize(o.stream);
     if (!st) st = cuda_status(e);
   }

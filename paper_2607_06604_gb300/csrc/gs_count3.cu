@@ -3,15 +3,21 @@
 //
 // For each hub i and spoke j in N+(i), the triangles (i, j, k) with k > j
 // are k in N+(i) intersected with N+(j). The paper walks both sorted lists
-// with two pointers per lane group; here a persistent CTA takes one hub at a
-// time, stages N+(i) in shared memory with a bulk (TMA) copy, builds a
-// shared-memory hash of it, and every warp streams the rows N+(j) of its
-// spokes with 128-bit loads, four edge words per lane, probing the hash.
-// A spoke row is read in ascending order and abandoned as soon as its ids
-// pass the largest id of N+(i) (the merge-walk's exhaustion rule).
-// Counts go to per-CTA shared-memory histograms over canonical
-// configurations and are flushed with one 64-bit atomic per bin.
-// Weighted sums use exact fixed point: per-triangle 128-bit products in
+// with two pointers; here one persistent 1024-thread CTA per SM takes one
+// hub at a time and stages N+(i) in shared memory with a bulk (TMA) copy.
+// Because ids are cell ordered, N+(i) lies in a short id span above i, so
+// the CTA writes every neighbour's bin into a shared byte table indexed by
+// id - (i + 1) (0xFF = not a neighbour). Each warp then streams the row
+// N+(j) of one spoke at a time with 128-bit loads (four edge words per
+// lane) and probes the table with one subtraction and one byte load; a
+// spoke row is abandoned as soon as its ids pass the largest id of N+(i)
+// (the merge-walk's exhaustion rule). Only the entries written are reset
+// afterwards. Hubs whose span exceeds the table (wrap-around neighbours of
+// a periodic box, very sparse catalogues) use a shared hash of N+(i) in
+// the same memory, staged in segments.
+// The configuration index comes from a shared table over (b_ij, b_ik, b_jk);
+// counts go to per-CTA shared-memory histograms flushed with one 64-bit
+// atomic per bin. Weighted sums use exact fixed point: 128-bit products in
 // shared 128-bit accumulators, flushed into 192-bit global accumulators.
 #include <algorithm>
 
@@ -20,73 +26,170 @@
 namespace gs {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kSegCap = 2048;   // hub-row words staged per pass
-constexpr int kHashCap = 8192;  // hash slots, >= 4 x staged words
+constexpr int kStageCap = 4096;   // hub-row words staged in shared memory
+constexpr int kSegCap = 2048;     // hash path: hub-row words per segment
+constexpr int kHashMax = 8192;    // hash path: slots, >= 4 x segment words
+constexpr int kLutMax = 16384;    // nb^3 entries of the configuration table
+constexpr uint8_t kAbsent = 0xFF;
 
-struct Args {
+// One catalogue's arrays. A batched launch carries one per catalogue.
+struct Cat {
   const int64_t* __restrict__ ptr;
   const int32_t* __restrict__ deg;
-  const uint32_t* __restrict__ adj;  // row i at adj + (ptr[i] - adj_off)
-  int64_t adj_off;
-  int64_t hub_begin, hub_end;
-  int nb, nconf;
-  int seg_cap;  // hub-row words staged per pass (<= kSegCap, multiple of 4)
+  const uint32_t* __restrict__ adj;  // row j at row_at(adj, ptr, j, adj_off, split, adj_off2)
+  int64_t adj_off, split, adj_off2;
+  const int64_t* __restrict__ W;
   unsigned long long* counts;  // [nconf]
   unsigned long long* wacc;    // [nconf][3] 192-bit
-  const int64_t* __restrict__ W;
+  int64_t hub_begin, hub_end;
+};
+
+struct Args {
+  Cat one;                // single-catalogue launches
+  const Cat* cats;        // batched launches: ncats catalogues whose hubs
+  const int64_t* base;    // form one queue; base[k] = first queue index of k
+  int ncats;
+  int nb, nconf;
+  int span_cap;           // bytes of the direct-address table (multiple of 16)
+  int seg_cap;            // hash path segment (<= kSegCap, multiple of 4)
+  int force_hash;         // 1: every hub takes the hash path
+  int stage_cap;          // hub rows up to this many words are staged
   unsigned long long* hub_counter;
   int* err;
 };
 
+struct Smem {
+  uint8_t* table;      // span_cap bytes; the hash path reuses it as words
+  uint32_t* stage;     // kStageCap words
+  uint16_t* lut;       // nb^3 configuration indices (or nullptr)
+  unsigned* hist;      // nconf
+  unsigned long long* whist;  // 2 nconf
+};
+
+__device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int nb) {
+  return sm.lut ? (int)sm.lut[(bij * nb + bik) * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
+}
+
 template <bool WEIGHTED, bool SMEM_HIST>
-__global__ void __launch_bounds__(kThreads) k_count3(Args a) {
+__device__ inline void record(const Smem& sm, const Cat& c, int cf, int64_t Wij, uint32_t k) {
+  if (SMEM_HIST) atomicAdd(sm.hist + cf, 1u);
+  else atomicAdd(c.counts + cf, 1ull);
+  if (WEIGHTED) {
+    long long lo, hi;
+    mul_i128(Wij, c.W[k], &lo, &hi);
+    if (SMEM_HIST) atomic_add_i128(sm.whist + 2 * cf, lo, hi);
+    else atomic_add_i192(c.wacc + 3 * cf, (unsigned long long)lo, (unsigned long long)hi);
+  }
+}
+
+template <bool WEIGHTED, bool SMEM_HIST, bool BATCH>
+__global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* stage = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* table = stage + kSegCap;
-  unsigned* hist = table + kHashCap;
-  unsigned long long* whist =
-      reinterpret_cast<unsigned long long*>(hist + ((a.nconf + 1) & ~1));
+  Smem sm;
+  {
+    unsigned char* p = smem;
+    sm.table = p;
+    p += a.span_cap;
+    sm.stage = reinterpret_cast<uint32_t*>(p);
+    p += kStageCap * 4;
+    const int nb3 = a.nb * a.nb * a.nb;
+    sm.lut = nb3 <= kLutMax ? reinterpret_cast<uint16_t*>(p) : nullptr;
+    if (sm.lut) p += ((nb3 * 2 + 15) / 16) * 16;
+    sm.hist = reinterpret_cast<unsigned*>(p);
+    p += ((a.nconf * 4 + 15) / 16) * 16;
+    sm.whist = reinterpret_cast<unsigned long long*>(p);
+  }
   __shared__ uint64_t bar;
   __shared__ int64_t s_hub;
   __shared__ unsigned long long s_pending;
-  __shared__ int s_flush;
+  __shared__ int s_flush, s_cat, s_cur, s_next;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = a.nb;
+  for (int k = tid; k < a.span_cap / 4; k += kThreads) reinterpret_cast<uint32_t*>(sm.table)[k] = kSentinel;
+  if (sm.lut)
+    for (int k = tid; k < nb * nb * nb; k += kThreads)
+      sm.lut[k] = (uint16_t)conf3_rank(k / (nb * nb), (k / nb) % nb, k % nb, nb);
   if (SMEM_HIST) {
-    for (int k = tid; k < a.nconf; k += kThreads) hist[k] = 0;
+    for (int k = tid; k < a.nconf; k += kThreads) sm.hist[k] = 0;
     if (WEIGHTED)
-      for (int k = tid; k < 2 * a.nconf; k += kThreads) whist[k] = 0;
+      for (int k = tid; k < 2 * a.nconf; k += kThreads) sm.whist[k] = 0;
   }
   if (tid == 0) {
     mbar_init(&bar, 1);
     s_pending = 0;
+    s_cur = BATCH ? -1 : 0;
   }
   __syncthreads();
   uint32_t phase = 0;
+  Cat c = a.one;
+  int cur = BATCH ? -1 : 0;
 
+  // shared histograms -> the current catalogue's global ones
   auto flush = [&]() {
-    if (!SMEM_HIST) return;
+    if (!SMEM_HIST || cur < 0) return;
     for (int k = tid; k < a.nconf; k += kThreads) {
-      const unsigned c = hist[k];
-      if (c) {
-        atomicAdd(a.counts + k, (unsigned long long)c);
-        hist[k] = 0;
+      const unsigned v = sm.hist[k];
+      if (v) {
+        atomicAdd(c.counts + k, (unsigned long long)v);
+        sm.hist[k] = 0;
+      }
+      if (WEIGHTED) {
+        const unsigned long long lo = sm.whist[2 * k], hi = sm.whist[2 * k + 1];
+        if (lo | hi) {
+          atomic_add_i192(c.wacc + 3 * k, lo, hi);
+          sm.whist[2 * k] = sm.whist[2 * k + 1] = 0;
+        }
       }
     }
+  };
+  // bounded wait on the bulk copy; false when it timed out (block-uniform)
+  auto wait_stage = [&]() -> bool {
+    const bool ok = mbar_wait(&bar, phase, kWaitLimit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(a.err, kErrTimeout);
+      return false;
+    }
+    return true;
   };
 
   for (;;) {
     if (tid == 0) {
-      s_hub = a.hub_begin + (int64_t)atomicAdd(a.hub_counter, 1ull);
+      const int64_t q = (int64_t)atomicAdd(a.hub_counter, 1ull);
+      int k = 0;
+      int64_t hub;
+      bool valid;
+      if (BATCH) {
+        valid = q < a.base[a.ncats];
+        if (valid) {
+          int lo = 0, hi = a.ncats;  // largest k with base[k] <= q
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.base[mid] <= q) lo = mid;
+            else hi = mid;
+          }
+          k = lo;
+        }
+        hub = valid ? q - a.base[k] : 0;
+      } else {
+        hub = a.one.hub_begin + q;
+        valid = hub < a.one.hub_end;
+      }
+      s_hub = valid ? hub : -1;
+      s_cat = k;
       s_flush = 0;
-      if (s_hub < a.hub_end) {
-        const unsigned long long d = (unsigned long long)a.deg[s_hub];
+      s_next = 0;
+      if (valid) {
+        const int32_t* dg = BATCH ? a.cats[k].deg : a.one.deg;
+        const unsigned long long d = (unsigned long long)dg[hub];
         const unsigned long long need = d * (d - (d > 0)) / 2;  // triangles at i <= C(d,2)
-        if (s_pending + need > 0xFFFFFFFFull) {
+        if (k != s_cur || s_pending + need > 0xFFFFFFFFull) {
           s_flush = 1;
           s_pending = need;
+          s_cur = k;
         } else {
           s_pending += need;
         }
@@ -94,53 +197,108 @@ __global__ void __launch_bounds__(kThreads) k_count3(Args a) {
     }
     __syncthreads();
     const int64_t i = s_hub;
-    if (i >= a.hub_end) break;
+    if (i < 0) break;
     if (s_flush) {
       flush();
       __syncthreads();
     }
-    const int d = a.deg[i];
+    if (BATCH && s_cat != cur) {
+      cur = s_cat;
+      c = a.cats[cur];
+    }
+    const int d = c.deg[i];
     if (d < 2) {
       __syncthreads();
       continue;
     }
-    const uint32_t* row = a.adj + (a.ptr[i] - a.adj_off);
-    const int64_t Wi = WEIGHTED ? a.W[i] : 0;
-    const int seg_cap = a.seg_cap;
+    const uint32_t* row = row_at(c.adj, c.ptr, i, c.adj_off, c.split, c.adj_off2);
+    const int64_t Wi = WEIGHTED ? c.W[i] : 0;
+    const uint32_t hub_hi = edge_id(row[d - 1]);
+    const int64_t span = (int64_t)hub_hi - i;  // ids i+1 .. hub_hi
+    const bool staged = d <= a.stage_cap;
+    if (!a.force_hash && span <= a.span_cap) {
+      // ---------------- direct-address table path
+      if (staged) {
+        if (tid == 0) bulk_load(sm.stage, row, (uint32_t)pad_row(d) * 4u, &bar);
+        if (!wait_stage()) return;
+      }
+      const uint32_t* hr = staged ? sm.stage : row;
+      const uint32_t base = (uint32_t)(i + 1);
+      for (int k = tid; k < d; k += kThreads) {
+        const uint32_t w = hr[k];
+        sm.table[edge_id(w) - base] = (uint8_t)edge_bin(w);
+      }
+      __syncthreads();
+      for (;;) {
+        int sp = 0;
+        if (lane == 0) sp = atomicAdd(&s_next, 1);
+        sp = __shfl_sync(0xffffffffu, sp, 0);
+        if (sp >= d - 1) break;  // the last neighbour has no k above it
+        const uint32_t wij = hr[sp];
+        const uint32_t j = edge_id(wij);
+        const int bij = (int)edge_bin(wij);
+        const int64_t Wij = WEIGHTED ? Wi * c.W[j] : 0;
+        const uint32_t* rj = row_at(c.adj, c.ptr, j, c.adj_off, c.split, c.adj_off2);
+        const int dj4 = (int)pad_row(c.deg[j]);
+        for (int t0 = 0; t0 < dj4; t0 += 128) {
+          const int t = t0 + lane * 4;
+          const uint4 v = (t < dj4) ? ldg_nc_v4(rj + t)
+                                    : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+          const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t key = edge_id(vv[q]);
+            if (key > hub_hi) continue;
+            const uint8_t bik = sm.table[key - base];
+            if (bik != kAbsent)
+              record<WEIGHTED, SMEM_HIST>(sm, c, conf_index(sm, bij, bik, (int)edge_bin(vv[q]), nb),
+                                          Wij, key);
+          }
+          const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+          if (edge_id(last) > hub_hi) break;
+        }
+      }
+      __syncthreads();
+      for (int k = tid; k < d; k += kThreads) sm.table[edge_id(hr[k]) - base] = kAbsent;
+      __syncthreads();
+      continue;
+    }
+    // ---------------- hash path (span wider than the table)
+    uint32_t* table = reinterpret_cast<uint32_t*>(sm.table);
+    const int tcap_bits = [&] {
+      int b = 7;
+      while ((2 << b) * 4 <= a.span_cap && b < 13) ++b;
+      return b;
+    }();
+    const int seg_cap = min(a.seg_cap, (1 << tcap_bits) / 4);
     for (int s0 = 0; s0 < d; s0 += seg_cap) {
       const int sn = min(seg_cap, d - s0);
       const int sn4 = (int)pad_row(sn);
-      if (tid == 0) bulk_load(stage, row + s0, (uint32_t)sn4 * 4u, &bar);
+      if (tid == 0) bulk_load(sm.stage, row + s0, (uint32_t)sn4 * 4u, &bar);
       int tbits = 7;
-      while ((1 << tbits) < 4 * sn && tbits < 13) ++tbits;
+      while ((1 << tbits) < 4 * sn && tbits < tcap_bits) ++tbits;
       const int T = 1 << tbits;
       const int shift = 32 - tbits;
-      for (int k = tid; k < T; k += kThreads) table[k] = kSentinel;
-      const bool ok = mbar_wait(&bar, phase, kWaitLimit);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicOr(a.err, kErrTimeout);
-        return;
-      }
+      if (!wait_stage()) return;
       for (int k = tid; k < sn; k += kThreads) {
-        const uint32_t w = stage[k];
+        const uint32_t w = sm.stage[k];
         uint32_t h = (edge_id(w) * kHashMul) >> shift;
         while (atomicCAS(table + h, kSentinel, w) != kSentinel) h = (h + 1) & (T - 1);
       }
       __syncthreads();
-      const uint32_t seg_lo = edge_id(stage[0]);
-      const uint32_t seg_hi = edge_id(stage[sn - 1]);
+      const uint32_t seg_lo = edge_id(sm.stage[0]);
+      const uint32_t seg_hi = edge_id(sm.stage[sn - 1]);
       for (int sp = warp; sp < d; sp += kWarps) {
-        const uint32_t wij = (d <= seg_cap) ? stage[sp] : row[sp];
+        const uint32_t wij = (d <= seg_cap) ? sm.stage[sp] : row[sp];
         const uint32_t j = edge_id(wij);
         if (j >= seg_hi) break;  // every k > j; none left in this segment
         const int bij = (int)edge_bin(wij);
-        const int64_t Wij = WEIGHTED ? Wi * a.W[j] : 0;
-        const uint32_t* rj = a.adj + (a.ptr[j] - a.adj_off);
-        const int dj4 = (int)pad_row(a.deg[j]);
+        const int64_t Wij = WEIGHTED ? Wi * c.W[j] : 0;
+        const uint32_t* rj = row_at(c.adj, c.ptr, j, c.adj_off, c.split, c.adj_off2);
+        const int dj4 = (int)pad_row(c.deg[j]);
         int start = 0;
         if (s0 > 0) {  // skip to the first id >= seg_lo (rows are sorted)
-          int lo = 0, hi = a.deg[j];
+          int lo = 0, hi = c.deg[j];
           const uint32_t key = seg_lo << 8;
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -163,15 +321,8 @@ __global__ void __launch_bounds__(kThreads) k_count3(Args a) {
               const uint32_t e = table[h];
               if (e == kSentinel) break;
               if (edge_id(e) == key) {
-                const int c = conf3_rank(bij, (int)edge_bin(e), (int)edge_bin(vv[q]), a.nb);
-                if (SMEM_HIST) atomicAdd(hist + c, 1u);
-                else atomicAdd(a.counts + c, 1ull);
-                if (WEIGHTED) {
-                  long long lo, hi;
-                  mul_i128(Wij, a.W[key], &lo, &hi);
-                  if (SMEM_HIST) atomic_add_i128(whist + 2 * c, lo, hi);
-                  else atomic_add_i192(a.wacc + 3 * c, (unsigned long long)lo, (unsigned long long)hi);
-                }
+                record<WEIGHTED, SMEM_HIST>(
+                    sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wij, key);
                 break;
               }
               h = (h + 1) & (T - 1);
@@ -182,16 +333,40 @@ __global__ void __launch_bounds__(kThreads) k_count3(Args a) {
         }
       }
       __syncthreads();
+      // restore the empty table (all bytes 0xFF) for the next hub
+      for (int k = tid; k < T; k += kThreads) table[k] = kSentinel;
+      __syncthreads();
     }
   }
   __syncthreads();
   flush();
-  if (SMEM_HIST && WEIGHTED) {
-    for (int k = tid; k < a.nconf; k += kThreads) {
-      const unsigned long long lo = whist[2 * k], hi = whist[2 * k + 1];
-      if (lo | hi) atomic_add_i192(a.wacc + 3 * k, lo, hi);
-    }
-  }
+}
+
+
+// Shared-memory layout of k_count3: the direct-address table takes what the
+// staging buffer, configuration table and histograms leave.
+struct Count3Launch {
+  size_t smem = 0;
+  int span_cap = 0;
+  bool smem_hist = true;
+};
+
+Count3Launch count3_launch(int nb, int nconf, bool weighted) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t nb3 = (size_t)nb * nb * nb;
+  const size_t lut = nb3 <= (size_t)kLutMax ? pad16(nb3 * 2) : 0;
+  size_t hist = pad16((size_t)nconf * 4) + (weighted ? (size_t)nconf * 16 : 0);
+  Count3Launch L;
+  const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
+  const size_t fixed = (size_t)kStageCap * 4 + lut;
+  L.smem_hist = fixed + hist + 32 * 1024 <= avail;
+  if (!L.smem_hist) hist = 0;
+  L.span_cap = (int)((avail - fixed - hist) & ~(size_t)15);
+  L.smem = (size_t)L.span_cap + fixed + hist;
+  return L;
 }
 
 }  // namespace
@@ -249,36 +424,46 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   cudaStream_t s = o.stream;
   const int nconf = (int)num_conf3(g.nb);
   Args a;
-  a.ptr = g.d_ptr;
-  a.deg = g.d_deg;
-  a.adj = nullptr;
-  a.adj_off = 0;
+  a.one.ptr = g.d_ptr;
+  a.one.deg = g.d_deg;
+  a.one.adj = nullptr;
+  a.one.adj_off = 0;
+  a.one.split = g.n;
+  a.one.adj_off2 = 0;
+  a.cats = nullptr;
+  a.base = nullptr;
+  a.ncats = 0;
   a.nb = g.nb;
   a.nconf = nconf;
-  // variant 1 stages 64-word segments: exercises the long-row path on any input
+  // variant 1: every hub through the hash path in 64-word segments;
+  // variant 2: the table path reading hub rows from global memory
   a.seg_cap = (o.variant & 1) ? 64 : kSegCap;
-  a.counts = reinterpret_cast<unsigned long long*>(d_counts);
-  a.W = fw ? fw->d_W : nullptr;
+  a.force_hash = (o.variant & 1) ? 1 : 0;
+  a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
+  a.force_hash = (o.variant & 1) ? 1 : 0;
+  a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
+  a.one.counts = reinterpret_cast<unsigned long long*>(d_counts);
+  a.one.W = fw ? fw->d_W : nullptr;
   const bool weighted = fw && d_wsum;
-  a.wacc = weighted ? sc.alloc<unsigned long long>(3 * (size_t)nconf) : nullptr;
+  a.one.wacc = weighted ? sc.alloc<unsigned long long>(3 * (size_t)nconf) : nullptr;
   a.hub_counter = sc.alloc<unsigned long long>(1);
   a.err = sc.alloc<int>(1);
-  if (!a.hub_counter || !a.err || (weighted && !a.wacc)) return GS_ENOMEM;
+  if (!a.hub_counter || !a.err || (weighted && !a.one.wacc)) return GS_ENOMEM;
   cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * nconf, s);
-  if (weighted) cudaMemsetAsync(a.wacc, 0, sizeof(unsigned long long) * 3 * nconf, s);
+  if (weighted) cudaMemsetAsync(a.one.wacc, 0, sizeof(unsigned long long) * 3 * nconf, s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   if (g.n == 0) {
     if (d_wsum) cudaMemsetAsync(d_wsum, 0, sizeof(double) * nconf, s);
     return cuda_status(cudaGetLastError());
   }
 
-  const size_t base = (size_t)(kSegCap + kHashCap) * 4;
-  const size_t hist_bytes = (size_t)((nconf + 1) & ~1) * 4 + (weighted ? (size_t)nconf * 16 : 0);
-  const bool smem_hist = hist_bytes <= 96 * 1024;
-  const size_t smem = base + (smem_hist ? hist_bytes : 0);
+  const Count3Launch L = count3_launch(g.nb, nconf, weighted);
+  a.span_cap = L.span_cap;
+  const bool smem_hist = L.smem_hist;
+  const size_t smem = L.smem;
   void (*kern)(Args);
-  if (weighted) kern = smem_hist ? k_count3<true, true> : k_count3<true, false>;
-  else kern = smem_hist ? k_count3<false, true> : k_count3<false, false>;
+  if (weighted) kern = smem_hist ? k_count3<true, true, false> : k_count3<true, false, false>;
+  else kern = smem_hist ? k_count3<false, true, false> : k_count3<false, false, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -287,12 +472,13 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   const int grid = std::max(1, per_sm) * sms;
   KernelTimer timer(o.kernel_ms);
   timer.start(s);
-  int st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
-                                         int64_t h1) -> int {
-    a.adj = adj;
-    a.adj_off = off;
-    a.hub_begin = h0;
-    a.hub_end = h1;
+  int st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+    a.one.adj = v.adj;
+    a.one.adj_off = v.off1;
+    a.one.split = v.split;
+    a.one.adj_off2 = v.off2;
+    a.one.hub_begin = v.h0;
+    a.one.hub_end = v.h1;
     cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
     { kern<<<grid, kThreads, smem, s>>>(a); note_launch(); }
     return cuda_status(cudaGetLastError());
@@ -302,9 +488,92 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   cudaError_t e;
   if (d_wsum) {
     if (weighted)
-      { k_i192_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(a.wacc, nconf, 3 * fw->scale, d_wsum); note_launch(); }
+      { k_i192_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(a.one.wacc, nconf, 3 * fw->scale, d_wsum); note_launch(); }
     else
-      { k_u64_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(a.counts, nconf, d_wsum); note_launch(); }
+      { k_u64_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(a.one.counts, nconf, d_wsum); note_launch(); }
+  }
+  int herr = 0;
+  cudaMemcpyAsync(&herr, a.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  timer.publish();
+  return herr ? GS_ETIMEOUT : GS_OK;
+}
+
+int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
+                        double* const* d_wsum, const Opts& o, Scratch& sc) {
+  cudaStream_t s = o.stream;
+  const int nb = gr[0]->nb;
+  const int nconf = (int)num_conf3(nb);
+  const bool weighted = fws != nullptr && d_wsum != nullptr;
+  std::vector<Cat> cats(ng);
+  std::vector<int64_t> base(ng + 1, 0);
+  unsigned long long* wacc =
+      weighted ? sc.alloc<unsigned long long>(3 * (size_t)nconf * ng) : nullptr;
+  if (weighted && !wacc) return GS_ENOMEM;
+  for (int k = 0; k < ng; ++k) {
+    const Graph& g = *gr[k];
+    Cat& c = cats[k];
+    c.ptr = g.d_ptr;
+    c.deg = g.d_deg;
+    c.adj = g.d_adj;
+    c.adj_off = 0;
+    c.split = g.n;
+    c.adj_off2 = 0;
+    c.W = weighted ? fws[k].d_W : nullptr;
+    c.counts = reinterpret_cast<unsigned long long*>(d_counts[k]);
+    c.wacc = weighted ? wacc + 3 * (size_t)nconf * k : nullptr;
+    c.hub_begin = 0;
+    c.hub_end = g.n;
+    base[k + 1] = base[k] + g.n;
+    cudaMemsetAsync(d_counts[k], 0, sizeof(uint64_t) * nconf, s);
+  }
+  if (weighted) cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * 3 * nconf * ng, s);
+  Cat* d_cats = sc.alloc<Cat>(ng);
+  int64_t* d_base = sc.alloc<int64_t>(ng + 1);
+  Args a;
+  a.one = cats[0];
+  a.cats = d_cats;
+  a.base = d_base;
+  a.ncats = ng;
+  a.nb = nb;
+  a.nconf = nconf;
+  a.seg_cap = (o.variant & 1) ? 64 : kSegCap;
+  a.force_hash = (o.variant & 1) ? 1 : 0;
+  a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
+  a.hub_counter = sc.alloc<unsigned long long>(1);
+  a.err = sc.alloc<int>(1);
+  if (!d_cats || !d_base || !a.hub_counter || !a.err) return GS_ENOMEM;
+  cudaMemcpyAsync(d_cats, cats.data(), sizeof(Cat) * ng, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(a.err, 0, sizeof(int), s);
+  const Count3Launch L = count3_launch(nb, nconf, weighted);
+  a.span_cap = L.span_cap;
+  const bool smem_hist = L.smem_hist;
+  const size_t smem = L.smem;
+  void (*kern)(Args);
+  if (weighted) kern = smem_hist ? k_count3<true, true, true> : k_count3<true, false, true>;
+  else kern = smem_hist ? k_count3<false, true, true> : k_count3<false, false, true>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0, sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  KernelTimer timer(o.kernel_ms);
+  timer.start(s);
+  if (base[ng] > 0) { kern<<<std::max(1, per_sm) * sms, kThreads, smem, s>>>(a); note_launch(); }
+  timer.stop(s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int k = 0; k < ng; ++k) {
+    if (!d_wsum || !d_wsum[k]) continue;
+    if (weighted)
+      { k_i192_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(wacc + 3 * (size_t)nconf * k, nconf,
+                                                           3 * fws[k].scale, d_wsum[k]); note_launch(); }
+    else
+      { k_u64_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(
+          reinterpret_cast<const unsigned long long*>(d_counts[k]), nconf, d_wsum[k]); note_launch(); }
   }
   int herr = 0;
   cudaMemcpyAsync(&herr, a.err, sizeof(int), cudaMemcpyDeviceToHost, s);

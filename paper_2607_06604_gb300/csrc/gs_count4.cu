@@ -35,8 +35,8 @@ constexpr int kMaxSmemRow = 512;
 struct Args {
   const int64_t* __restrict__ ptr;
   const int32_t* __restrict__ deg;
-  const uint32_t* __restrict__ adj;  // row i at adj + (ptr[i] - adj_off)
-  int64_t adj_off;
+  const uint32_t* __restrict__ adj;  // row i at row_at(adj, ptr, i, adj_off, split, adj_off2)
+  int64_t adj_off, split, adj_off2;
   int64_t hub_begin, hub_end;
   const int4* __restrict__ xyzp;
   const int64_t* __restrict__ e2g;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     }
     const int m = a.deg[i];
     const int W = (m + 31) / 32;
-    const uint32_t* grow = a.adj + (a.ptr[i] - a.adj_off);
+    const uint32_t* grow = row_at(a.adj, a.ptr, i, a.adj_off, a.split, a.adj_off2);
     const uint32_t* row = w.row;
     if (!BIG) {
       if (tid == 0) bulk_load(w.row, grow, (uint32_t)pad_row(m) * 4u, &bar);
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     const uint32_t hub_hi = edge_id(row[m - 1]);
     for (int sa = warp; sa < m - 1; sa += kWarps) {
       const uint32_t j = edge_id(row[sa]);
-      const uint32_t* rj = a.adj + (a.ptr[j] - a.adj_off);
+      const uint32_t* rj = row_at(a.adj, a.ptr, j, a.adj_off, a.split, a.adj_off2);
       const int dj4 = (int)pad_row(a.deg[j]);
       for (int t0 = 0; t0 < dj4; t0 += 128) {
         const int t = t0 + lane * 4;
@@ -372,6 +372,8 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   a.deg = g.d_deg;
   a.adj = nullptr;
   a.adj_off = 0;
+  a.split = g.n;
+  a.adj_off2 = 0;
   a.hub_begin = 0;
   a.hub_end = g.n;
   a.xyzp = g.d_xyzp;
@@ -440,12 +442,13 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   }
   KernelTimer timer(o.kernel_ms);
   timer.start(s);
-  st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
-                                     int64_t h1) -> int {
-    a.adj = adj;
-    a.adj_off = off;
-    a.hub_begin = h0;
-    a.hub_end = h1;
+  st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+    a.adj = v.adj;
+    a.adj_off = v.off1;
+    a.split = v.split;
+    a.adj_off2 = v.off2;
+    a.hub_begin = v.h0;
+    a.hub_end = v.h1;
     cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long) * 2, s);
     // launch 1: rows up to mcap, workspace in shared memory
     if (!force_global) {

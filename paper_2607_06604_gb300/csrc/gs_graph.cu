@@ -427,11 +427,29 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
     }
     std::vector<int32_t> hdeg(n);
     cudaMemcpy(hdeg.data(), g->d_deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    // first id of the last x-slab (cells are x-major); open boxes: n
+    g->wrap_start = n;
+    if (box_u) {
+      int32_t ws = 0;
+      const int64_t c_last = (int64_t)(G.nc[0] - 1) * G.nc[1] * G.nc[2];
+      cudaMemcpy(&ws, start + c_last, sizeof(int32_t), cudaMemcpyDeviceToHost);
+      g->wrap_start = ws;
+    }
     g->h_reach.resize(n);
-    for (int64_t i = 0; i < n; ++i)
-      g->h_reach[i] = hdeg[i] ? (int32_t)edge_id(g->h_adj[g->h_ptr[i] + hdeg[i] - 1]) : (int32_t)i;
+    g->h_far.assign(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      const uint32_t* r = g->h_adj + g->h_ptr[i];
+      int d = hdeg[i];
+      if (i < g->wrap_start) {  // split off the wrap-around neighbours
+        int e = d;
+        while (e > 0 && (int64_t)edge_id(r[e - 1]) >= g->wrap_start) --e;
+        g->h_far[i] = (e < d) ? 1 : 0;
+        d = e;
+      }
+      g->h_reach[i] = d ? (int32_t)edge_id(r[d - 1]) : (int32_t)i;
+    }
     WindowPlan plan;
-    st = plan_windows(*g, o, &plan);
+    st = plan_windows(*g, o, &plan, 0, n);
     if (st) return st;
     g->windows = (int)plan.h0.size();
   }
@@ -450,8 +468,9 @@ namespace {
 // walk[i] summed: for each edge (i, j), the words of N+(j) with id <= the
 // largest id of N+(i).
 __global__ void k_walk_words(const int32_t* __restrict__ deg, const int64_t* __restrict__ ptr,
-                             const uint32_t* __restrict__ adj, int64_t adj_off, int64_t h0,
-                             int64_t h1, unsigned long long* total) {
+                             const uint32_t* __restrict__ adj, int64_t adj_off, int64_t split,
+                             int64_t adj_off2, int64_t h0, int64_t h1,
+                             unsigned long long* total) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   unsigned long long acc = 0;
@@ -459,11 +478,11 @@ __global__ void k_walk_words(const int32_t* __restrict__ deg, const int64_t* __r
        i += warps) {
     const int d = deg[i];
     if (d == 0) continue;
-    const uint32_t* r = adj + (ptr[i] - adj_off);
+    const uint32_t* r = row_at(adj, ptr, i, adj_off, split, adj_off2);
     const uint32_t hub_hi = edge_id(r[d - 1]);
     for (int k = lane; k < d; k += 32) {
       const uint32_t j = edge_id(r[k]);
-      const uint32_t* rj = adj + (ptr[j] - adj_off);
+      const uint32_t* rj = row_at(adj, ptr, j, adj_off, split, adj_off2);
       int lo = 0, hi = deg[j];
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -488,10 +507,9 @@ int walk_words_device(Graph* g) {
   unsigned long long* tot = sc.alloc<unsigned long long>(1);
   if (!tot) return GS_ENOMEM;
   cudaMemsetAsync(tot, 0, sizeof(unsigned long long), o.stream);
-  int st = for_each_window(*g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
-                                          int64_t h1) -> int {
-    { k_walk_words<<<grid_blocks((h1 - h0) * 32, 256), 256, 0, o.stream>>>(g->d_deg, g->d_ptr, adj, off, h0, h1,
-                                                                     tot); note_launch(); }
+  int st = for_each_window(*g, o, sc, [&](const WinView& v) -> int {
+    { k_walk_words<<<grid_blocks((v.h1 - v.h0) * 32, 256), 256, 0, o.stream>>>(
+        g->d_deg, g->d_ptr, v.adj, v.off1, v.split, v.off2, v.h0, v.h1, tot); note_launch(); }
     return cuda_status(cudaGetLastError());
   });
   if (st) return st;
@@ -503,35 +521,65 @@ int walk_words_device(Graph* g) {
   return GS_OK;
 }
 
-int plan_windows(const Graph& g, const Opts& o, WindowPlan* plan) {
-  const int64_t n = g.n;
+void shard_range(const Graph& g, const Opts& o, int64_t* lo, int64_t* hi) {
+  *lo = 0;
+  *hi = g.n;
+  if (o.shards <= 1 || g.n == 0) return;
+  // boundaries at equal shares of the edge words (h_ptr is nondecreasing)
+  const int64_t total = g.h_ptr[g.n];
+  auto bound = [&](int k) -> int64_t {
+    if (k <= 0) return 0;
+    if (k >= o.shards) return g.n;
+    const int64_t target = (int64_t)((__int128)total * k / o.shards);
+    return std::lower_bound(g.h_ptr.begin(), g.h_ptr.begin() + g.n, target) - g.h_ptr.begin();
+  };
+  *lo = bound(o.shard);
+  *hi = bound(o.shard + 1);
+}
+
+int plan_windows(const Graph& g, const Opts& o, WindowPlan* plan, int64_t lo, int64_t hi) {
   const std::vector<int64_t>& P = g.h_ptr;
-  const int64_t slots = P[n];
+  const int64_t n = g.n, ws = g.wrap_start;
+  const int64_t far_words = P[n] - P[ws];
   // a query without its own budget / window count uses the graph's
   const uint64_t budget = o.budget ? o.budget : g.budget;
   const int force = o.force_windows > 0 ? o.force_windows : g.force_windows;
   const int64_t cap = budget ? (int64_t)(budget / (2 * sizeof(uint32_t))) : INT64_MAX;
-  const int64_t target = force > 0 ? (slots + force - 1) / force : INT64_MAX;
+  const int64_t target = force > 0 ? (P[hi] - P[lo] + force - 1) / force : INT64_MAX;
+  // words a window [h0, h1) with near reach r and far flag f needs
+  auto need = [&](int64_t h0, int64_t r, bool f) -> int64_t {
+    if (f && r >= ws) return P[n] - P[h0];  // the two ranges touch: one range
+    return (P[r] - P[h0]) + (f ? far_words : 0);
+  };
   plan->h0.clear();
   plan->h1.clear();
   plan->r1.clear();
+  plan->far.clear();
   plan->max_words = 0;
-  int64_t h0 = 0;
-  while (h0 < n) {
+  int64_t h0 = lo;
+  while (h0 < hi) {
     int64_t h1 = h0, reach = h0 + 1;
-    while (h1 < n) {
-      const int64_t nr = std::max<int64_t>(std::max<int64_t>(reach, (int64_t)g.h_reach[h1] + 1), h1 + 1);
+    bool far = false;
+    while (h1 < hi) {
+      const int64_t nr =
+          std::max<int64_t>(std::max<int64_t>(reach, (int64_t)g.h_reach[h1] + 1), h1 + 1);
+      const bool nf = far || g.h_far[h1];
       const int64_t own = P[h1 + 1] - P[h0];
-      const int64_t need = P[nr] - P[h0];
-      if (h1 > h0 && (own > target || need > cap)) break;
+      if (h1 > h0 && (own > target || need(h0, nr, nf) > cap)) break;
       reach = nr;
+      far = nf;
       ++h1;
     }
-    const int64_t words = P[reach] - P[h0];
+    const int64_t words = need(h0, reach, far);
     if (words > cap) return GS_ENOMEM;  // one hub's rows exceed a window buffer
+    if (far && reach >= ws) {
+      reach = n;
+      far = false;
+    }
     plan->h0.push_back(h0);
     plan->h1.push_back(h1);
     plan->r1.push_back(reach);
+    plan->far.push_back(far ? 1 : 0);
     plan->max_words = std::max(plan->max_words, words);
     h0 = h1;
   }

@@ -61,7 +61,14 @@ struct Graph {
   uint32_t* d_adj = nullptr;    // [slots] packed edge words (resident graphs)
   uint32_t* h_adj = nullptr;    // [slots] pinned host copy (out-of-core graphs)
   std::vector<int64_t> h_ptr;   // host copy of d_ptr (window planning)
-  std::vector<int32_t> h_reach; // out-of-core: largest id in N+(i), or i when empty
+  // out-of-core planning. In a periodic box the ids are x-major, so hubs
+  // of the first x-slab have wrap-around neighbours in the last one:
+  // wrap_start is the first id of the last x-slab (n for an open box);
+  // h_reach[i] is the largest neighbour id of i below wrap_start (or i) and
+  // h_far[i] says whether i has neighbours at or above wrap_start.
+  std::vector<int32_t> h_reach;
+  std::vector<uint8_t> h_far;
+  int64_t wrap_start = 0;
   int64_t slots = 0;
   int64_t edges_total = 0;
   int64_t probe_words = 0;
@@ -82,7 +89,11 @@ struct Opts {
   int variant = 0;
   cudaStream_t stream = nullptr;
   double* kernel_ms = nullptr;
+  int shard = 0, shards = 0;
 };
+
+// Hub range [lo, hi) of the query's shard (the whole graph when unsharded).
+void shard_range(const Graph& g, const Opts& o, int64_t* lo, int64_t* hi);
 Opts read_opts(const gs_options* o);
 
 // Whether p is device-accessible memory of the current device.
@@ -148,34 +159,60 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
                        const std::vector<int64_t>& edges, const Opts& o, Graph* g);
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
                   const Opts& o, Scratch& sc);
+int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
+                        double* const* d_wsum, const Opts& o, Scratch& sc);
 int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
                   int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc);
 int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint64_t* d_pairs,
                       double* d_xi, double* d_zeta, const Opts& o, Scratch& sc);
 int walk_words_device(Graph* g);
+int quantize_device(const double* d_pos, int64_t n, int64_t box_u, int periodic, int32_t* d_xyz,
+                    cudaStream_t s, Scratch& sc);
 
 // ----------------------------------------------------------------------------
-// Out-of-core row windows. Window k covers hubs [h0, h1); the rows it needs
-// (the hubs' own rows and every spoke row) are the contiguous range
-// [h0, r1) with r1 = 1 + the largest neighbour id of the window's hubs,
-// because every spoke id is above its hub. Each hub belongs to exactly one
-// window, so every tuple is counted exactly once.
+// Out-of-core row windows. Window k covers hubs [h0, h1). The rows it needs
+// (the hubs' own rows and every spoke row) are at most two id ranges,
+// because every spoke id is above its hub: [h0, r1) with r1 = 1 + the
+// largest neighbour id below wrap_start, plus [wrap_start, n) when a hub
+// has wrap-around neighbours. Each hub belongs to exactly one window, so
+// every tuple is counted exactly once.
 struct WindowPlan {
   std::vector<int64_t> h0, h1, r1;
+  std::vector<uint8_t> far;  // the window also needs rows [wrap_start, n)
   int64_t max_words = 0;
 };
-int plan_windows(const Graph& g, const Opts& o, WindowPlan* plan);
+int plan_windows(const Graph& g, const Opts& o, WindowPlan* plan, int64_t lo, int64_t hi);
+
+// Where the rows of one window live: row j starts at
+// adj + ptr[j] - (j >= split ? off2 : off1).
+struct WinView {
+  const uint32_t* adj;
+  int64_t off1, split, off2;
+  int64_t h0, h1;
+};
+
+__host__ __device__ inline const uint32_t* row_at(const uint32_t* adj, const int64_t* ptr,
+                                                  int64_t j, int64_t off1, int64_t split,
+                                                  int64_t off2) {
+  return adj + (ptr[j] - (j >= split ? off2 : off1));
+}
 
 // Streams the windows of an out-of-core graph through two device buffers:
 // the copy of window k+1 (pinned host -> device, on a side stream) overlaps
-// the counting of window k on o.stream. fn(adj, adj_off, h0, h1) launches
-// the counting for hubs [h0, h1) with row i at adj + (ptr[i] - adj_off).
-// A resident graph makes one call with its own edge array.
+// the counting of window k on o.stream. fn(const WinView&) launches the
+// counting of the window's hubs. A resident graph makes one call with its
+// own edge array.
 template <class F>
 int for_each_window(const Graph& g, const Opts& o, Scratch& sc, F&& fn) {
-  if (g.d_adj) return fn(static_cast<const uint32_t*>(g.d_adj), (int64_t)0, (int64_t)0, g.n);
+  int64_t lo = 0, hi = 0;
+  shard_range(g, o, &lo, &hi);
+  if (lo >= hi) return GS_OK;
+  if (g.d_adj) {
+    const WinView v{g.d_adj, 0, g.n, 0, lo, hi};
+    return fn(v);
+  }
   WindowPlan plan;
-  int st = plan_windows(g, o, &plan);
+  int st = plan_windows(g, o, &plan, lo, hi);
   if (st) return st;
   const size_t nw = plan.h0.size();
   uint32_t* buf[2] = {sc.alloc<uint32_t>(plan.max_words),
@@ -189,6 +226,7 @@ int for_each_window(const Graph& g, const Opts& o, Scratch& sc, F&& fn) {
     e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
   }
+  const int64_t n = g.n;
   if (e == cudaSuccess) {
     // the buffers were allocated in o.stream's order
     cudaEventRecord(ready, o.stream);
@@ -196,14 +234,22 @@ int for_each_window(const Graph& g, const Opts& o, Scratch& sc, F&& fn) {
     for (size_t k = 0; k < nw && !st; ++k) {
       const int b = (int)(k & 1);
       if (k >= 2) cudaStreamWaitEvent(cs, done[b], 0);
-      const int64_t off = g.h_ptr[plan.h0[k]];
-      const int64_t words = g.h_ptr[plan.r1[k]] - off;
-      e = cudaMemcpyAsync(buf[b], g.h_adj + off, sizeof(uint32_t) * words,
-                          cudaMemcpyHostToDevice, cs);
+      const int64_t off1 = g.h_ptr[plan.h0[k]];
+      const int64_t len1 = g.h_ptr[plan.r1[k]] - off1;
+      e = cudaMemcpyAsync(buf[b], g.h_adj + off1, sizeof(uint32_t) * len1, cudaMemcpyHostToDevice,
+                          cs);
+      WinView v{buf[b], off1, n, 0, plan.h0[k], plan.h1[k]};
+      if (e == cudaSuccess && plan.far[k]) {
+        const int64_t w0 = g.h_ptr[g.wrap_start];
+        e = cudaMemcpyAsync(buf[b] + len1, g.h_adj + w0, sizeof(uint32_t) * (g.h_ptr[n] - w0),
+                            cudaMemcpyHostToDevice, cs);
+        v.split = g.wrap_start;
+        v.off2 = w0 - len1;
+      }
       if (e != cudaSuccess) break;
       cudaEventRecord(copied[b], cs);
       cudaStreamWaitEvent(o.stream, copied[b], 0);
-      st = fn(static_cast<const uint32_t*>(buf[b]), off, plan.h0[k], plan.h1[k]);
+      st = fn(v);
       cudaEventRecord(done[b], o.stream);
     }
     cudaStreamSynchronize(cs);
@@ -217,8 +263,6 @@ int for_each_window(const Graph& g, const Opts& o, Scratch& sc, F&& fn) {
   if (cs) cudaStreamDestroy(cs);
   return st;
 }
-int quantize_device(const double* d_pos, int64_t n, int64_t box_u, int periodic, int32_t* d_xyz,
-                    cudaStream_t s, Scratch& sc);
 
 // Device helpers shared by the counting kernels --------------------------------
 

@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(kThreads) k_pairs_count(const uint4* __restric
 // moments sum W_i and sum W_i^2 (for the analytic random pair count).
 __global__ void __launch_bounds__(kThreads) k_pairs_weighted(
     const int64_t* __restrict__ ptr, const int32_t* __restrict__ deg,
-    const uint32_t* __restrict__ adj, int64_t adj_off, const int64_t* __restrict__ W,
-    int64_t h0, int64_t h1, int nb, unsigned long long* pairs, unsigned long long* wpairs,
-    unsigned long long* moments) {
+    const uint32_t* __restrict__ adj, int64_t adj_off, int64_t split, int64_t adj_off2,
+    const int64_t* __restrict__ W, int64_t h0, int64_t h1, int nb, unsigned long long* pairs,
+    unsigned long long* wpairs, unsigned long long* moments) {
   __shared__ unsigned long long acc[2 * (kMaxBins + 1)];
   __shared__ unsigned cnt[kMaxBins + 1];
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs_weighted(
        i += warps) {
     const int64_t Wi = W[i];
     const int d = deg[i];
-    const uint32_t* r = adj + (ptr[i] - adj_off);
+    const uint32_t* r = row_at(adj, ptr, i, adj_off, split, adj_off2);
     for (int k = lane; k < d; k += 32) {
       const uint32_t w = r[k];
       const int b = (int)edge_bin(w);
@@ -153,10 +153,10 @@ int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint
     cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * (3 * nb + 6), s);
     timer.start(s);
     if (g.n)
-      st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
-                                         int64_t h1) -> int {
-        { k_pairs_weighted<<<sms * 8, kThreads, 0, s>>>(g.d_ptr, g.d_deg, adj, off, fw->d_W, h0,
-                                                      h1, nb, pairs, wacc, wacc + 3 * nb); note_launch(); }
+      st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+        { k_pairs_weighted<<<sms * 8, kThreads, 0, s>>>(g.d_ptr, g.d_deg, v.adj, v.off1, v.split, v.off2,
+                                                      fw->d_W, v.h0, v.h1, nb, pairs, wacc,
+                                                      wacc + 3 * nb); note_launch(); }
         return cuda_status(cudaGetLastError());
       });
     timer.stop(s);
@@ -168,11 +168,12 @@ int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint
   } else if (g.slots) {
     timer.start(s);
     // the own rows of a window are its first ptr[h1] - ptr[h0] words
-    st = for_each_window(g, o, sc, [&](const uint32_t* adj, int64_t off, int64_t h0,
-                                       int64_t h1) -> int {
-      const int64_t words = g.h_ptr[h1] - g.h_ptr[h0];
+    st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+      // the window's own rows are contiguous from row h0 (below any split)
+      const int64_t words = g.h_ptr[v.h1] - g.h_ptr[v.h0];
+      const uint32_t* own = v.adj + (g.h_ptr[v.h0] - v.off1);
       if (words)
-        { k_pairs_count<<<sms * 8, kThreads, 0, s>>>(reinterpret_cast<const uint4*>(adj), words / 4, nb,
+        { k_pairs_count<<<sms * 8, kThreads, 0, s>>>(reinterpret_cast<const uint4*>(own), words / 4, nb,
                                                    pairs); note_launch(); }
       return cuda_status(cudaGetLastError());
     });

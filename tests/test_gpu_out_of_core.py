@@ -71,15 +71,19 @@ def test_forced_windows_bit_identical(gs, case, resident, windows):
 def test_budget_driven_windows(gs, case, resident):
     X, box_u, edges, w = case
     slots = resident["info"]["edge_slots"]
-    budget = slots * 4 // 3  # forces at least two windows of half that size
+    # two window buffers of 40% of the edges each: own rows plus the next
+    # x-slab plus the wrap-around slab fit, the whole graph does not
+    budget = int(slots * 4 * 0.8)
     g = gs.gs_build_graph(X, box_u, edges, budget=budget)
     info = gs.gs_graph_info(g)
     assert info["windows"] >= 2
     c, ws = gs.gs_count_3pcf(g, w)
     assert np.array_equal(c, resident["c3"][0]) and np.array_equal(ws, resident["c3"][1])
     # a query may ask for smaller windows than the build did
-    c2 = gs.gs_count_3pcf(g, budget=budget // 2)
+    c2 = gs.gs_count_3pcf(g, budget=int(budget * 0.75))
     assert np.array_equal(c2, resident["c3"][0])
+    e, o = gs.gs_count_4pcf_parity(g)
+    assert np.array_equal(e, resident["c4"][0]) and np.array_equal(o, resident["c4"][1])
 
 
 def test_budget_too_small(gs, case):
@@ -90,3 +94,26 @@ def test_budget_too_small(gs, case):
     # the library stays usable after the error
     g = gs.gs_build_graph(X[:1000], box_u, edges)
     assert gs.gs_count_3pcf(g).sum() >= 0
+
+
+@pytest.mark.parametrize("shards,windows", [(2, 0), (3, 0), (4, 3)])
+def test_hub_shards_sum_exactly(gs, case, resident, shards, windows):
+    """Hub shards (the multi-GPU split of one catalogue) run one after
+    another on this GPU; their counts add up to the unsharded result."""
+    X, box_u, edges, w = case
+    g = gs.gs_build_graph(X, box_u, edges, force_windows=windows)
+    c3 = sum(gs.gs_count_3pcf(g, shard=k, shards=shards).astype(np.int64) for k in range(shards))
+    assert np.array_equal(c3, resident["c3"][0].astype(np.int64))
+    e = np.zeros_like(resident["c4"][0], dtype=np.int64)
+    o = np.zeros_like(resident["c4"][1])
+    p = np.zeros(len(edges) - 1, dtype=np.int64)
+    for k in range(shards):
+        ek, ok = gs.gs_count_4pcf_parity(g, shard=k, shards=shards)
+        e += ek.astype(np.int64)
+        o += ok
+        p += gs.gs_disconnected_4pcf(g, zeta=False, shard=k, shards=shards)[0].astype(np.int64)
+    assert np.array_equal(e, resident["c4"][0].astype(np.int64))
+    assert np.array_equal(o, resident["c4"][1])
+    assert np.array_equal(p, resident["pairs"][0].astype(np.int64))
+    ws = sum(gs.gs_count_3pcf(g, w, shard=k, shards=shards)[1] for k in range(shards))
+    np.testing.assert_allclose(ws, resident["c3"][1], rtol=1e-14)

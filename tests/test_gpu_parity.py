@@ -170,6 +170,13 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     np.testing.assert_allclose(gw, rw, rtol=RTOL, atol=0)
     # unweighted call on the same graph agrees with the weighted call's counts
     assert np.array_equal(run3(gs, torch_mod, X, bu, edges), rc)
+    # every kernel path gives the same answer: hash path in 64-word segments
+    # (variant 1) and the table path reading hub rows from global (variant 2)
+    g = gs.gs_build_graph(X, bu, edges)
+    for variant in (1, 2):
+        vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
+        assert np.array_equal(vc, rc), variant
+        assert np.array_equal(vw, gw), variant
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
