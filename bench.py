@@ -51,8 +51,13 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-4pcf", action="store_true",
                     help="skip the secondary 4pCF + parity measurement")
-    ap.add_argument("--profile", choices=["count3", "count4", "pairs"], default=None,
+    ap.add_argument("--profile", choices=["count3", "count3w", "count4", "pairs"], default=None,
                     help="run one small case of one kernel for an ncu capture (no JSON)")
+    ap.add_argument("--mocks", type=int, default=0,
+                    help="also serve this many lognormal mock catalogues (request loop)")
+    ap.add_argument("--mock-nmax", type=float, default=4e5)
+    ap.add_argument("--ooc", action="store_true",
+                    help="also measure the out-of-core overhead on the 1e6-point rmax-150 workload")
     return ap.parse_args()
 
 
@@ -344,6 +349,8 @@ def run_ours(args):
     quad = None
     if not args.no_4pcf:
         quad = measure_4pcf(gs, torch)
+    mocks = measure_mocks(gs, torch, args.mocks, args.mock_nmax) if args.mocks else None
+    ooc = measure_ooc(gs, torch) if args.ooc else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -359,6 +366,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "quadruplets": quad,
+            "mocks": mocks, "out_of_core": ooc,
             "graph_randoms": {k2: info[k2] for k2 in ("edges", "max_degree", "probe_words",
                                                       "walk_words", "edge_slots")}}
     print(json.dumps(line), flush=True)
@@ -397,13 +405,126 @@ def measure_4pcf(gs, torch, runs=2):
             "odd_abs_sum": float(odd.abs().sum().item())}
 
 
+def make_mocks(count, nmax, seed=11):
+    """Lognormal mock ensemble: sizes log-uniform in [5e4, nmax], L = 500,
+    3pCF rmax 60 in 12 bins; the first 32 also ask for the 4pCF (rmax 25,
+    6 bins). A 128^3 field keeps host generation to a fraction of a second
+    per catalogue."""
+    import oracle  # noqa: F401  (not used: quantisation below is the library's)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(np.log(5e4), np.log(nmax), size=count)).astype(int)
+    L = 500.0
+    out = []
+    for k, n in enumerate(sizes):
+        pos = catalogs.lognormal(int(n), L, seed=seed * 1000 + k, grid=128)
+        out.append(pos)
+    return out, sizes, L
+
+
+def measure_mocks(gs, torch, count, nmax):
+    L = 500.0
+    box_u = int(L * 1024)
+    e3 = catalogs.bin_edges_u(0.0, 60.0, 12)
+    e4 = catalogs.bin_edges_u(0.0, 25.0, 6)
+    t_gen = time.perf_counter()
+    mocks, sizes, _ = make_mocks(count, nmax)
+    t_gen = time.perf_counter() - t_gen
+    xyz = [gs.gs_quantize(p, box_u, True) for p in mocks]
+    kinds = [4 if k < 32 else 3 for k in range(count)]
+    # a) one catalogue at a time through the plain API
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for k, X in enumerate(xyz):
+        g = gs.gs_build_graph(X, box_u, e3)
+        plain.append(gs.gs_count_3pcf(g))
+        g.close()
+        if kinds[k] == 4:
+            g4 = gs.gs_build_graph(X, box_u, e4)
+            gs.gs_count_4pcf_parity(g4)
+            g4.close()
+    t_plain = time.perf_counter() - t0
+    tri = float(sum(int(c.sum()) for c in plain))
+
+    def serve(rate):
+        lat, res = [], {}
+        rng = np.random.default_rng(5)
+        with gs.gs_server() as srv:
+            t_start = time.perf_counter()
+            tickets = []
+            for k, X in enumerate(xyz):
+                if rate:
+                    time.sleep(rng.exponential(1.0 / rate))
+                tickets.append((k, srv.submit(X, box_u, e3, npoint=3)))
+                if kinds[k] == 4:
+                    tickets.append((-1 - k, srv.submit(X, box_u, e4, npoint=4)))
+            for k, t in tickets:
+                c, o, ws, info = srv.wait(t)
+                lat.append(info["t_done"] - info["t_submit"])
+                res[k] = c
+            span = time.perf_counter() - t_start
+        return span, np.array(lat), res
+
+    t_sat, lat_sat, res = serve(0.0)
+    same = all(np.array_equal(res[k], plain[k]) for k in range(count))
+    capacity = count / t_sat
+    t_poi, lat_poi, res2 = serve(0.8 * capacity)
+    same = same and all(np.array_equal(res2[k], plain[k]) for k in range(count))
+    return {"catalogues": count, "n_range": [int(sizes.min()), int(sizes.max())],
+            "box": L, "rmax3": 60.0, "nb3": 12, "rmax4": 25.0, "nb4": 6, "also_4pcf": min(32, count),
+            "triangles": tri, "host_generation_s": t_gen,
+            "one_at_a_time_s": t_plain, "one_at_a_time_catalogues_per_s": count / t_plain,
+            "served_saturated_s": t_sat, "served_catalogues_per_s": capacity,
+            "speedup_vs_one_at_a_time": t_plain / t_sat,
+            "poisson_rate_per_s": 0.8 * capacity, "poisson_span_s": t_poi,
+            "latency_p50_s": float(np.percentile(lat_poi, 50)),
+            "latency_p99_s": float(np.percentile(lat_poi, 99)),
+            "saturated_latency_p50_s": float(np.percentile(lat_sat, 50)),
+            "saturated_latency_p99_s": float(np.percentile(lat_sat, 99)),
+            "results_identical_to_single_calls": bool(same)}
+
+
+def measure_ooc(gs, torch):
+    """Out-of-core overhead on 1e6 Neyman-Scott points (sigma 5) in an open
+    box L = 1494, rmax 150 in 15 bins, under a 16 GB device graph budget and
+    with forced window counts: t(windows) / t(resident) - 1."""
+    import ctypes
+    spec = catalogs.draw("ns1M_open_L1494_r150_nb15")
+    box_u, edges = spec["box_u"], spec["edges_u"]
+    X = gs.gs_quantize(torch.from_numpy(spec["pos"]).cuda(), box_u, False)
+    out = {"workload": "ns1M_open_L1494_r150_nb15", "budget_bytes": 16 << 30}
+    base = None
+    for label, kw in (("resident", {}), ("budget_16GB", {"budget": 16 << 30}),
+                      ("W2", {"force_windows": 2}), ("W4", {"force_windows": 4}),
+                      ("W8", {"force_windows": 8})):
+        g = gs.gs_build_graph(X, 0, edges, **kw)
+        info = gs.gs_graph_info(g)
+        km = ctypes.c_double(0.0)
+        t0 = time.perf_counter()
+        c = gs.gs_count_3pcf(g, like=X, kernel_ms=km)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if base is None:
+            base = c.cpu().numpy()
+            out["edges"] = info["edges"]
+            out["graph_bytes"] = info["edge_slots"] * 4
+            out["triangles"] = float(base.sum())
+        same = bool(np.array_equal(c.cpu().numpy(), base))
+        out[label] = {"windows": info["windows"], "query_s": dt, "kernel_ms": km.value,
+                      "identical": same}
+        g.close()
+    for label in ("budget_16GB", "W2", "W4", "W8"):
+        out[label]["overhead"] = out[label]["query_s"] / out["resident"]["query_s"] - 1.0
+    return out
+
+
 def run_profile(args):
     """One small case per kernel, sized above L2 but a few GB at most."""
     import torch
 
     import paper_2607_06604_gb300 as gs
     torch.cuda.set_device(0)
-    if args.profile in ("count3", "pairs"):
+    if args.profile in ("count3", "count3w", "pairs"):
         # 1e6 uniform points at the randoms' density (3e-3 per (h^-1 Mpc)^3),
         # rmax 40 in 20 bins: a 1.6 GB graph
         L = 693.0
@@ -411,9 +532,12 @@ def run_profile(args):
         pos = torch.from_numpy(catalogs.uniform(1_000_000, L, seed=5)).cuda()
         edges = catalogs.bin_edges_u(0.0, 40.0, 20)
         g = gs.gs_build_graph(gs.gs_quantize(pos, box_u, True), box_u, edges)
+        w = torch.from_numpy(catalogs.uniform_weights(1_000_000, seed=6)).cuda()
         for _ in range(2):
             if args.profile == "count3":
                 gs.gs_count_3pcf(g, like=pos)
+            elif args.profile == "count3w":
+                gs.gs_count_3pcf(g, w)
             else:
                 gs.gs_disconnected_4pcf(g, like=pos, zeta=False)
     else:

@@ -177,6 +177,25 @@ int gs_count_3pcf_batch(const gs_graph* const* graphs, int32_t n_graphs, const f
                         uint64_t* const* counts, double* const* wsum, const gs_options* options);
 
 /*
+ * Recorded batched launches. gs_plan_3pcf_batch records one unweighted
+ * batched 3pCF count of fixed resident graphs (clearing the outputs and the
+ * persistent kernel) into a CUDA graph; gs_plan_launch replays it on a
+ * stream, asynchronously, with no allocation and no host synchronisation;
+ * gs_plan_wait synchronises the stream and returns GS_ETIMEOUT if the last
+ * replay's kernel reported an expired wait. The graphs must outlive the
+ * plan; counts are n_graphs DEVICE arrays of C(nb+2,3) uint64 rewritten by
+ * every replay. Replays of one plan must not overlap each other on the GPU.
+ * Errors: GS_EINVAL (NULL, unequal nb, out-of-core graph, host outputs),
+ * GS_ENOMEM, GS_ECUDA.
+ */
+typedef struct gs_plan gs_plan;
+int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graphs, uint64_t* const* counts,
+                       const gs_options* options, gs_plan** out);
+int gs_plan_launch(gs_plan* plan, void* stream);
+int gs_plan_wait(gs_plan* plan, void* stream);
+void gs_plan_destroy(gs_plan* plan);
+
+/*
  * gs_count_4pcf - binned tetrahedron counts (Sec. 2.2, Sec. 3.1.1):
  * tetrahedra whose six pairs are all edges, one count per S4 orbit.
  *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact).

@@ -24,7 +24,7 @@ __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
     "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_3pcf_batch", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_num_configs", "gs_config_bins",
-    "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "lib_path",
+    "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
 ]
 
 
@@ -84,6 +84,10 @@ def _load():
         "gs_count_3pcf": ([P, P, P, P, OP], ci),
         "gs_count_4pcf": ([P, P, P, P, OP], ci),
         "gs_count_3pcf_batch": ([P, ctypes.c_int32, P, P, P, OP], ci),
+        "gs_plan_3pcf_batch": ([P, ctypes.c_int32, P, OP, ctypes.POINTER(P)], ci),
+        "gs_plan_launch": ([P, P], ci),
+        "gs_plan_wait": ([P, P], ci),
+        "gs_plan_destroy": ([P], None),
         "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
         "gs_num_configs": ([ci, ci, ctypes.POINTER(i64)], ci),
@@ -363,6 +367,45 @@ class gs_server:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class gs_plan:
+    """A batched 3pCF count recorded once into a CUDA graph and replayed
+    (gs_plan_* in the C ABI). Outputs are torch CUDA tensors kept here."""
+
+    def __init__(self, graphs, **opts):
+        import torch
+        self._graphs = list(graphs)  # the plan refers to them
+        nc = gs_num_configs(3, self._graphs[0].nb)
+        self.counts = [torch.zeros(nc, dtype=torch.uint64, device="cuda") for _ in self._graphs]
+        n = len(self._graphs)
+        P = ctypes.c_void_p
+        harr = (P * n)(*[g.handle for g in self._graphs])
+        carr = (P * n)(*[_ptr(c) for c in self.counts])
+        o = _options(**opts)
+        self._h = ctypes.c_void_p()
+        _check(_lib.gs_plan_3pcf_batch(harr, n, carr, ctypes.byref(o), ctypes.byref(self._h)),
+               "gs_plan_3pcf_batch")
+
+    def launch(self, stream=None):
+        s = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(_lib.gs_plan_launch(self._h, s), "gs_plan_launch")
+
+    def wait(self, stream=None):
+        s = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(_lib.gs_plan_wait(self._h, s), "gs_plan_wait")
+        return self.counts
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gs_plan_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

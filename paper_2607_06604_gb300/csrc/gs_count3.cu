@@ -56,13 +56,15 @@ struct Args {
   int seg_cap;            // hash path segment (<= kSegCap, multiple of 4)
   int force_hash;         // 1: every hub takes the hash path
   int stage_cap;          // hub rows up to this many words are staged
+  int stage_alloc;        // words of the staging buffer
   unsigned long long* hub_counter;
   int* err;
 };
 
 struct Smem {
   uint8_t* table;      // span_cap bytes; the hash path reuses it as words
-  uint32_t* stage;     // kStageCap words
+  uint32_t* stage;     // stage_alloc words
+  int64_t* wst;        // weighted: stage_alloc staged weights of N+(i)
   uint16_t* lut;       // nb^3 configuration indices (or nullptr)
   unsigned* hist;      // nconf
   unsigned long long* whist;  // 2 nconf
@@ -73,12 +75,12 @@ __device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int 
 }
 
 template <bool WEIGHTED, bool SMEM_HIST>
-__device__ inline void record(const Smem& sm, const Cat& c, int cf, int64_t Wij, uint32_t k) {
+__device__ inline void record(const Smem& sm, const Cat& c, int cf, int64_t Wij, int64_t Wk) {
   if (SMEM_HIST) atomicAdd(sm.hist + cf, 1u);
   else atomicAdd(c.counts + cf, 1ull);
   if (WEIGHTED) {
     long long lo, hi;
-    mul_i128(Wij, c.W[k], &lo, &hi);
+    mul_i128(Wij, Wk, &lo, &hi);
     if (SMEM_HIST) atomic_add_i128(sm.whist + 2 * cf, lo, hi);
     else atomic_add_i192(c.wacc + 3 * cf, (unsigned long long)lo, (unsigned long long)hi);
   }
@@ -93,7 +95,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     sm.table = p;
     p += a.span_cap;
     sm.stage = reinterpret_cast<uint32_t*>(p);
-    p += kStageCap * 4;
+    p += (size_t)a.stage_alloc * 4;
+    sm.wst = reinterpret_cast<int64_t*>(p);
+    if (WEIGHTED) p += (size_t)a.stage_alloc * 8;
     const int nb3 = a.nb * a.nb * a.nb;
     sm.lut = nb3 <= kLutMax ? reinterpret_cast<uint16_t*>(p) : nullptr;
     if (sm.lut) p += ((nb3 * 2 + 15) / 16) * 16;
@@ -105,10 +109,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   __shared__ int64_t s_hub;
   __shared__ unsigned long long s_pending;
   __shared__ int s_flush, s_cat, s_cur, s_next;
+  __shared__ int s_warp_sum[kWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = a.nb;
-  for (int k = tid; k < a.span_cap / 4; k += kThreads) reinterpret_cast<uint32_t*>(sm.table)[k] = kSentinel;
+  // idle table: all bytes 0xFF (byte table) or all bits clear (weighted bitmap)
+  const uint32_t idle = WEIGHTED ? 0u : kSentinel;
+  for (int k = tid; k < a.span_cap / 4; k += kThreads) reinterpret_cast<uint32_t*>(sm.table)[k] = idle;
   if (sm.lut)
     for (int k = tid; k < nb * nb * nb; k += kThreads)
       sm.lut[k] = (uint16_t)conf3_rank(k / (nb * nb), (k / nb) % nb, k % nb, nb);
@@ -216,50 +223,140 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     const uint32_t hub_hi = edge_id(row[d - 1]);
     const int64_t span = (int64_t)hub_hi - i;  // ids i+1 .. hub_hi
     const bool staged = d <= a.stage_cap;
-    if (!a.force_hash && span <= a.span_cap) {
+    // weighted hubs need their row and weights staged (positions come from
+    // the bitmap rank); the bitmap + 16-bit prefix take 6 bytes per 32 ids
+    const int64_t table_span = WEIGHTED ? (int64_t)(a.span_cap / 6) * 32 : (int64_t)a.span_cap;
+    if (!a.force_hash && span <= table_span && (!WEIGHTED || staged)) {
       // ---------------- direct-address table path
       if (staged) {
         if (tid == 0) bulk_load(sm.stage, row, (uint32_t)pad_row(d) * 4u, &bar);
+        if (WEIGHTED)
+          for (int k = tid; k < d; k += kThreads) sm.wst[k] = c.W[edge_id(row[k])];
         if (!wait_stage()) return;
       }
       const uint32_t* hr = staged ? sm.stage : row;
       const uint32_t base = (uint32_t)(i + 1);
-      for (int k = tid; k < d; k += kThreads) {
-        const uint32_t w = hr[k];
-        sm.table[edge_id(w) - base] = (uint8_t)edge_bin(w);
+      uint32_t* bm = reinterpret_cast<uint32_t*>(sm.table);
+      const int nw = (int)((span + 31) >> 5);
+      uint16_t* pre = reinterpret_cast<uint16_t*>(bm + nw);
+      if (WEIGHTED) {
+        for (int k = tid; k < d; k += kThreads) {
+          const uint32_t off = edge_id(hr[k]) - base;
+          atomicOr(bm + (off >> 5), 1u << (off & 31));
+        }
+        __syncthreads();
+        // exclusive prefix of the words' popcounts: the rank of every bit
+        const int per = (nw + kThreads - 1) / kThreads;
+        const int w0 = min(nw, tid * per), w1 = min(nw, w0 + per);
+        int sum = 0;
+        for (int q = w0; q < w1; ++q) sum += __popc(bm[q]);
+        int x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+          int t = s_warp_sum[lane];
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+          }
+          s_warp_sum[lane] = t;
+        }
+        __syncthreads();
+        int run = x - sum + (warp ? s_warp_sum[warp - 1] : 0);
+        for (int q = w0; q < w1; ++q) {
+          pre[q] = (uint16_t)run;
+          run += __popc(bm[q]);
+        }
+      } else {
+        for (int k = tid; k < d; k += kThreads) {
+          const uint32_t w = hr[k];
+          sm.table[edge_id(w) - base] = (uint8_t)edge_bin(w);
+        }
       }
       __syncthreads();
-      for (;;) {
-        int sp = 0;
-        if (lane == 0) sp = atomicAdd(&s_next, 1);
-        sp = __shfl_sync(0xffffffffu, sp, 0);
-        if (sp >= d - 1) break;  // the last neighbour has no k above it
-        const uint32_t wij = hr[sp];
-        const uint32_t j = edge_id(wij);
-        const int bij = (int)edge_bin(wij);
-        const int64_t Wij = WEIGHTED ? Wi * c.W[j] : 0;
-        const uint32_t* rj = row_at(c.adj, c.ptr, j, c.adj_off, c.split, c.adj_off2);
-        const int dj4 = (int)pad_row(c.deg[j]);
-        for (int t0 = 0; t0 < dj4; t0 += 128) {
-          const int t = t0 + lane * 4;
-          const uint4 v = (t < dj4) ? ldg_nc_v4(rj + t)
-                                    : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+      // Each warp walks spoke rows in 128-word chunks; the next chunk, or the
+      // first chunk of the warp's next spoke, is loaded before the current
+      // one is probed.
+      const uint4 none = make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+      int sp = 0;
+      if (lane == 0) sp = atomicAdd(&s_next, 1);
+      sp = __shfl_sync(0xffffffffu, sp, 0);
+      if (sp < d - 1) {  // the last neighbour has no k above it
+        uint32_t wij = hr[sp];
+        const uint32_t* rj = row_at(c.adj, c.ptr, edge_id(wij), c.adj_off, c.split, c.adj_off2);
+        int dj4 = (int)pad_row(c.deg[edge_id(wij)]);
+        int t0 = 0;
+        uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
+        for (;;) {
+          const int bij = (int)edge_bin(wij);
+          const int64_t Wij = WEIGHTED ? Wi * (staged ? sm.wst[sp] : c.W[edge_id(wij)]) : 0;
+          const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+          const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
+          uint4 vn = none;
+          int nsp = sp;
+          uint32_t nwij = wij;
+          const uint32_t* nrj = rj;
+          int ndj4 = dj4;
+          if (more) {
+            const int t = t0 + 128 + lane * 4;
+            vn = (t < dj4) ? ldg_nc_v4(rj + t) : none;
+          } else {
+            if (lane == 0) nsp = atomicAdd(&s_next, 1);
+            nsp = __shfl_sync(0xffffffffu, nsp, 0);
+            if (nsp < d - 1) {
+              nwij = hr[nsp];
+              nrj = row_at(c.adj, c.ptr, edge_id(nwij), c.adj_off, c.split, c.adj_off2);
+              ndj4 = (int)pad_row(c.deg[edge_id(nwij)]);
+              vn = (lane * 4 < ndj4) ? ldg_nc_v4(nrj + lane * 4) : none;
+            }
+          }
           const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const uint32_t key = edge_id(vv[q]);
             if (key > hub_hi) continue;
-            const uint8_t bik = sm.table[key - base];
-            if (bik != kAbsent)
-              record<WEIGHTED, SMEM_HIST>(sm, c, conf_index(sm, bij, bik, (int)edge_bin(vv[q]), nb),
-                                          Wij, key);
+            const uint32_t off = key - base;
+            if (WEIGHTED) {
+              const uint32_t bw = bm[off >> 5];
+              const uint32_t bit = 1u << (off & 31);
+              if (bw & bit) {
+                const int pos = (int)pre[off >> 5] + __popc(bw & (bit - 1u));
+                record<WEIGHTED, SMEM_HIST>(
+                    sm, c, conf_index(sm, bij, (int)edge_bin(hr[pos]), (int)edge_bin(vv[q]), nb),
+                    Wij, sm.wst[pos]);
+              }
+            } else {
+              const uint8_t bik = sm.table[off];
+              if (bik != kAbsent)
+                record<WEIGHTED, SMEM_HIST>(sm, c, conf_index(sm, bij, bik, (int)edge_bin(vv[q]), nb),
+                                            0, 0);
+            }
           }
-          const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
-          if (edge_id(last) > hub_hi) break;
+          if (more) {
+            t0 += 128;
+          } else {
+            if (nsp >= d - 1) break;
+            sp = nsp;
+            wij = nwij;
+            rj = nrj;
+            dj4 = ndj4;
+            t0 = 0;
+          }
+          v = vn;
         }
       }
       __syncthreads();
-      for (int k = tid; k < d; k += kThreads) sm.table[edge_id(hr[k]) - base] = kAbsent;
+      if (WEIGHTED) {
+        // the next hub's bitmap may extend over this hub's prefix words
+        for (int k = tid; k < d; k += kThreads) bm[(edge_id(hr[k]) - base) >> 5] = 0u;
+        for (int q = tid; q < (nw + 1) / 2; q += kThreads) bm[nw + q] = 0u;
+      } else {
+        for (int k = tid; k < d; k += kThreads) sm.table[edge_id(hr[k]) - base] = kAbsent;
+      }
       __syncthreads();
       continue;
     }
@@ -279,6 +376,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       while ((1 << tbits) < 4 * sn && tbits < tcap_bits) ++tbits;
       const int T = 1 << tbits;
       const int shift = 32 - tbits;
+      if (WEIGHTED)
+        for (int k = tid; k < T; k += kThreads) table[k] = kSentinel;
       if (!wait_stage()) return;
       for (int k = tid; k < sn; k += kThreads) {
         const uint32_t w = sm.stage[k];
@@ -322,7 +421,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               if (e == kSentinel) break;
               if (edge_id(e) == key) {
                 record<WEIGHTED, SMEM_HIST>(
-                    sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wij, key);
+                    sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wij,
+                    WEIGHTED ? c.W[key] : 0);
                 break;
               }
               h = (h + 1) & (T - 1);
@@ -333,8 +433,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         }
       }
       __syncthreads();
-      // restore the empty table (all bytes 0xFF) for the next hub
-      for (int k = tid; k < T; k += kThreads) table[k] = kSentinel;
+      // restore the idle table for the next hub
+      for (int k = tid; k < T; k += kThreads) table[k] = idle;
       __syncthreads();
     }
   }
@@ -348,10 +448,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
 struct Count3Launch {
   size_t smem = 0;
   int span_cap = 0;
+  int stage_words = 0;
   bool smem_hist = true;
 };
 
 Count3Launch count3_launch(int nb, int nconf, bool weighted) {
+  // weighted launches stage rows and weights of up to 2048 neighbours
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -361,10 +463,12 @@ Count3Launch count3_launch(int nb, int nconf, bool weighted) {
   size_t hist = pad16((size_t)nconf * 4) + (weighted ? (size_t)nconf * 16 : 0);
   Count3Launch L;
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
-  const size_t fixed = (size_t)kStageCap * 4 + lut;
+  const size_t stage_words = weighted ? 2048 : kStageCap;
+  const size_t fixed = stage_words * (weighted ? 12 : 4) + lut;
   L.smem_hist = fixed + hist + 32 * 1024 <= avail;
   if (!L.smem_hist) hist = 0;
   L.span_cap = (int)((avail - fixed - hist) & ~(size_t)15);
+  L.stage_words = (int)stage_words;
   L.smem = (size_t)L.span_cap + fixed + hist;
   return L;
 }
@@ -440,8 +544,6 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   a.seg_cap = (o.variant & 1) ? 64 : kSegCap;
   a.force_hash = (o.variant & 1) ? 1 : 0;
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
-  a.force_hash = (o.variant & 1) ? 1 : 0;
-  a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.one.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.one.W = fw ? fw->d_W : nullptr;
   const bool weighted = fw && d_wsum;
@@ -459,6 +561,8 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
 
   const Count3Launch L = count3_launch(g.nb, nconf, weighted);
   a.span_cap = L.span_cap;
+  a.stage_alloc = L.stage_words;
+  a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
@@ -550,6 +654,8 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   const Count3Launch L = count3_launch(nb, nconf, weighted);
   a.span_cap = L.span_cap;
+  a.stage_alloc = L.stage_words;
+  a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
@@ -584,3 +690,130 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
 }
 
 }  // namespace gs
+
+// ----------------------------------------------------------------------------
+// Recorded batched launches. A plan uploads the catalogue descriptors once,
+// records the launch sequence of one batched count (clearing the outputs,
+// the persistent kernel) into a CUDA graph, and replays it on request:
+// repeated queries on resident catalogues then cost one graph launch, with
+// no allocation and no host synchronisation per replay.
+struct gs_plan {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* d_cats = nullptr;
+  int64_t* d_base = nullptr;
+  unsigned long long* counter = nullptr;
+  int* err = nullptr;
+};
+
+extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graphs,
+                                  uint64_t* const* counts, const gs_options* options,
+                                  gs_plan** out) {
+  using namespace gs;
+  if (!graphs || !counts || !out || n_graphs < 1) return GS_EINVAL;
+  *out = nullptr;
+  const int nb = graphs[0] ? graphs[0]->g.nb : 0;
+  for (int k = 0; k < n_graphs; ++k) {
+    if (!graphs[k] || !counts[k] || graphs[k]->g.nb != nb || !graphs[k]->g.d_adj) return GS_EINVAL;
+    if (!is_device_ptr(counts[k])) return GS_EINVAL;
+  }
+  const Opts o = read_opts(options);
+  const int nconf = (int)num_conf3(nb);
+  gs_plan* P = new (std::nothrow) gs_plan();
+  if (!P) return GS_ENOMEM;
+  std::vector<Cat> cats(n_graphs);
+  std::vector<int64_t> base(n_graphs + 1, 0);
+  for (int k = 0; k < n_graphs; ++k) {
+    const Graph& g = graphs[k]->g;
+    Cat& c = cats[k];
+    c.ptr = g.d_ptr;
+    c.deg = g.d_deg;
+    c.adj = g.d_adj;
+    c.adj_off = 0;
+    c.split = g.n;
+    c.adj_off2 = 0;
+    c.W = nullptr;
+    c.counts = reinterpret_cast<unsigned long long*>(counts[k]);
+    c.wacc = nullptr;
+    c.hub_begin = 0;
+    c.hub_end = g.n;
+    base[k + 1] = base[k] + g.n;
+  }
+  cudaError_t e = cudaMalloc(&P->d_cats, sizeof(Cat) * n_graphs);
+  if (e == cudaSuccess) e = cudaMalloc(&P->d_base, sizeof(int64_t) * (n_graphs + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&P->counter, sizeof(unsigned long long) + sizeof(int) + 8);
+  if (e == cudaSuccess) {
+    P->err = reinterpret_cast<int*>(P->counter + 1);
+    e = cudaMemcpy(P->d_cats, cats.data(), sizeof(Cat) * n_graphs, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(P->d_base, base.data(), sizeof(int64_t) * (n_graphs + 1), cudaMemcpyHostToDevice);
+  Args a;
+  a.one = cats[0];
+  a.cats = static_cast<const Cat*>(P->d_cats);
+  a.base = P->d_base;
+  a.ncats = n_graphs;
+  a.nb = nb;
+  a.nconf = nconf;
+  a.seg_cap = (o.variant & 1) ? 64 : kSegCap;
+  a.force_hash = (o.variant & 1) ? 1 : 0;
+  a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
+  a.hub_counter = P->counter;
+  a.err = P->err;
+  const Count3Launch L = count3_launch(nb, nconf, false);
+  a.span_cap = L.span_cap;
+  a.stage_alloc = L.stage_words;
+  a.stage_cap = std::min(a.stage_cap, L.stage_words);
+  void (*kern)(Args) = L.smem_hist ? k_count3<false, true, true> : k_count3<false, false, true>;
+  int per_sm = 0, sms = 0, dev = 0;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.smem);
+  cudaStream_t s = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(P->counter, 0, sizeof(unsigned long long) + sizeof(int), s);
+    for (int k = 0; k < n_graphs; ++k) cudaMemsetAsync(counts[k], 0, sizeof(uint64_t) * nconf, s);
+    if (base[n_graphs] > 0) kern<<<std::max(1, per_sm) * sms, kThreads, L.smem, s>>>(a);
+    cudaError_t ce = cudaStreamEndCapture(s, &P->graph);
+    e = (e == cudaSuccess) ? ce : e;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+  if (s) cudaStreamDestroy(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    gs_plan_destroy(P);
+    return cuda_status(e);
+  }
+  *out = P;
+  return GS_OK;
+}
+
+extern "C" int gs_plan_launch(gs_plan* P, void* stream) {
+  if (!P || !P->exec) return GS_EINVAL;
+  const cudaError_t e = cudaGraphLaunch(P->exec, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) gs::note_launch();
+  return gs::cuda_status(e);
+}
+
+extern "C" int gs_plan_wait(gs_plan* P, void* stream) {
+  if (!P) return GS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return gs::cuda_status(e);
+  return herr ? GS_ETIMEOUT : GS_OK;
+}
+
+extern "C" void gs_plan_destroy(gs_plan* P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  cudaFree(P->d_cats);
+  cudaFree(P->d_base);
+  cudaFree(P->counter);
+  delete P;
+}

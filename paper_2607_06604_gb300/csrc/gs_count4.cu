@@ -84,7 +84,7 @@ struct Workspace {
   int4* disp;         // displacement of each neighbour from the hub
   unsigned long long* table;  // hash: (id << 32) | local index, empty = ~0
   uint32_t* bits;     // m x W bit matrix
-  uint16_t* queue;    // per-warp (a, b) queue: kWarps x 64
+  uint32_t* queue;    // per-warp (b, c) queue: kWarps x 64 words, then kWarps x 64 bytes
 };
 
 template <bool PARITY, bool WEIGHTED, bool BIG>
@@ -118,9 +118,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     p += (size_t)(1 << tcap_bits) * 8;
     w.bits = reinterpret_cast<uint32_t*>(p);
     p += (size_t)mcap * Wcap * 4;
-    w.queue = reinterpret_cast<uint16_t*>(p);
+    w.queue = reinterpret_cast<uint32_t*>(p);
   }
-  uint16_t* q = w.queue + warp * 64;
 
   for (int k = tid; k < a.n_orbits; k += kThreads) {
     h_even[k] = 0;
@@ -247,93 +246,109 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
       }
     }
     __syncthreads();
-    // tetrahedra: warp per row a; (a, b) pairs queued 32 at a time
+    // tetrahedra: warp per row a, triangles (a, b) in a warp-uniform loop;
+    // the common neighbours c > b of a and b are compacted into a per-warp
+    // queue of (b, c) entries that carries over between triangles, and each
+    // batch of 32 entries is processed one tetrahedron per lane
     const int64_t Wi = WEIGHTED ? a.W[i] : 0;
+    uint32_t* qbc = w.queue + warp * 64;
+    uint8_t* qb12 = reinterpret_cast<uint8_t*>(w.queue + kWarps * 64) + warp * 64;
     for (int sa = warp; sa < m - 2; sa += kWarps) {
       const uint32_t wa = row[sa];
       const int b01 = (int)edge_bin(wa);
       const int4 da = w.disp[sa];
       const int64_t Wia = WEIGHTED ? Wi * a.W[edge_id(wa)] : 0;
-      int qn = 0;
       const uint32_t* bra = w.bits + sa * W;
-      for (int wd = sa >> 5; wd <= W; ++wd) {
-        uint32_t x = 0;
-        if (wd < W) x = bra[wd];
-        const bool drain = (wd == W);
-        const bool set = (x >> lane) & 1u;
-        const unsigned m_set = __ballot_sync(0xffffffffu, set);
-        if (set) q[qn + __popc(m_set & ((1u << lane) - 1u))] = (uint16_t)(wd * 32 + lane);
-        qn += __popc(m_set);
-        __syncwarp();
-        while (qn >= 32 || (drain && qn > 0)) {
+      int qn = 0;
+      // process the first 32 queue entries (or all when draining)
+      auto drain = [&](bool all) {
+        while (qn >= 32 || (all && qn > 0)) {
           const bool active = lane < qn;
-          const int sb = active ? q[lane] : 0;
+          const uint32_t e = active ? qbc[lane] : 0u;
+          const int b12 = active ? (int)qb12[lane] : 0;
           __syncwarp();
           if (active) {
-            const uint32_t wb = row[sb];
-            const int b02 = (int)edge_bin(wb);
-            const int4 db = w.disp[sb];
-            const int b12 = bin_of(d2(da, db), e2, nb);
-            const uint32_t* lrow = a.lut + (size_t)((b01 * nb + b02) * nb + b12) * nb * nb * nb;
-            const uint32_t* brb = w.bits + sb * W;
-            const int64_t Wb = WEIGHTED ? a.W[edge_id(wb)] : 0;
-            for (int wc = sb >> 5; wc < W; ++wc) {
-              uint32_t x2 = bra[wc] & brb[wc];
-              if (wc == (sb >> 5)) x2 &= ~((2u << (sb & 31)) - 1u);
-              while (x2) {
-                const int sc = wc * 32 + __ffs(x2) - 1;
-                x2 &= x2 - 1u;
-                const uint32_t wcw = row[sc];
-                const int4 dc = w.disp[sc];
-                const int b03 = (int)edge_bin(wcw);
-                const int b13 = bin_of(d2(da, dc), e2, nb);
-                const int b23 = bin_of(d2(db, dc), e2, nb);
-                const uint32_t ent = lrow[(b03 * nb + b13) * nb + b23];
-                const int orbit = (int)(ent & 0x3FFFFFFFu);
-                if (BIG) atomicAdd(a.even + orbit, 1ull);
-                else atomicAdd(h_even + orbit, 1u);
-                long long plo = 0, phi = 0;
-                // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
-                if (WEIGHTED) mul_i128(Wia, Wb * a.W[edge_id(wcw)], &plo, &phi);
-                if (WEIGHTED)
-                  atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
-                if (PARITY && (ent >> 31)) {
-                  const int64_t V =
-                      (int64_t)da.x * ((int64_t)db.y * dc.z - (int64_t)db.z * dc.y) -
-                      (int64_t)da.y * ((int64_t)db.x * dc.z - (int64_t)db.z * dc.x) +
-                      (int64_t)da.z * ((int64_t)db.x * dc.y - (int64_t)db.y * dc.x);
-                  if (V != 0) {
-                    int sgn = V > 0 ? 1 : -1;
-                    if ((ent >> 30) & 1u) sgn = -sgn;
-                    if (BIG) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
-                    else atomicAdd(h_odd + orbit, sgn);
-                    if (WEIGHTED) {
-                      unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
-                      if (sgn < 0) {  // negate the 128-bit product
-                        lo = ~lo + 1ull;
-                        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-                      }
-                      atomic_add_i192(a.wodd + 3 * orbit, lo, hi);
-                    }
+            const int sb = (int)(e >> 16), sc = (int)(e & 0xFFFFu);
+            const uint32_t wb = row[sb], wcw = row[sc];
+            const int4 db = w.disp[sb], dc = w.disp[sc];
+            const int b02 = (int)edge_bin(wb), b03 = (int)edge_bin(wcw);
+            const int b13 = bin_of(d2(da, dc), e2, nb);
+            const int b23 = bin_of(d2(db, dc), e2, nb);
+            const uint32_t ent =
+                a.lut[(((size_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
+            const int orbit = (int)(ent & 0x3FFFFFFFu);
+            if (BIG) atomicAdd(a.even + orbit, 1ull);
+            else atomicAdd(h_even + orbit, 1u);
+            long long plo = 0, phi = 0;
+            // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
+            if (WEIGHTED) {
+              mul_i128(Wia, a.W[edge_id(wb)] * a.W[edge_id(wcw)], &plo, &phi);
+              atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
+            }
+            if (PARITY && (ent >> 31)) {
+              const int64_t V = (int64_t)da.x * ((int64_t)db.y * dc.z - (int64_t)db.z * dc.y) -
+                                (int64_t)da.y * ((int64_t)db.x * dc.z - (int64_t)db.z * dc.x) +
+                                (int64_t)da.z * ((int64_t)db.x * dc.y - (int64_t)db.y * dc.x);
+              if (V != 0) {
+                int sgn = V > 0 ? 1 : -1;
+                if ((ent >> 30) & 1u) sgn = -sgn;
+                if (BIG) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
+                else atomicAdd(h_odd + orbit, sgn);
+                if (WEIGHTED) {
+                  unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
+                  if (sgn < 0) {  // negate the 128-bit product
+                    lo = ~lo + 1ull;
+                    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
                   }
+                  atomic_add_i192(a.wodd + 3 * orbit, lo, hi);
                 }
               }
             }
           }
-          if (qn >= 32) {
-            // move the overflow entries (queue holds at most 63)
+          if (qn >= 32) {  // keep the overflow (the queue holds at most 63)
             const int rest = qn - 32;
-            uint16_t mv = 0;
-            if (lane < rest) mv = q[32 + lane];
+            uint32_t mv = 0;
+            uint8_t mb = 0;
+            if (lane < rest) {
+              mv = qbc[32 + lane];
+              mb = qb12[32 + lane];
+            }
             __syncwarp();
-            if (lane < rest) q[lane] = mv;
+            if (lane < rest) {
+              qbc[lane] = mv;
+              qb12[lane] = mb;
+            }
             __syncwarp();
             qn = rest;
           } else {
             qn = 0;
           }
         }
+      };
+      for (int wb0 = sa >> 5; wb0 < W; ++wb0) {
+        uint32_t xb = bra[wb0];
+        while (xb) {  // warp-uniform: every lane walks the same bits
+          const int sb = wb0 * 32 + __ffs(xb) - 1;
+          xb &= xb - 1u;
+          const int b12 = bin_of(d2(da, w.disp[sb]), e2, nb);
+          const uint32_t* brb = w.bits + sb * W;
+          for (int wc = sb >> 5; wc < W; ++wc) {
+            uint32_t x = bra[wc] & brb[wc];
+            if (wc == (sb >> 5)) x &= ~((2u << (sb & 31)) - 1u);
+            if (!x) continue;
+            const bool set = (x >> lane) & 1u;
+            if (set) {
+              const int slot = qn + __popc(x & ((1u << lane) - 1u));
+              qbc[slot] = ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
+              qb12[slot] = (uint8_t)b12;
+            }
+            qn += __popc(x);
+            __syncwarp();
+            drain(false);
+          }
+        }
       }
+      drain(true);
     }
     __syncthreads();
   }
@@ -346,7 +361,7 @@ size_t workspace_bytes(int mcap) {
   while ((1 << tbits) < 2 * mcap) ++tbits;
   const size_t Wc = (size_t)(mcap + 31) / 32;
   return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + ((size_t)1 << tbits) * 8 +
-         (size_t)mcap * Wc * 4 + (size_t)kWarps * 64 * 2 + 64;
+         (size_t)mcap * Wc * 4 + (size_t)kWarps * 64 * 5 + 64;
 }
 
 }  // namespace

@@ -374,3 +374,4 @@ constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a wait gives up
 struct gs_graph {
   gs::Graph g;
 };
+struct gs_plan;
