@@ -162,6 +162,28 @@ int gs_count_3pcf(const gs_graph* g, const float* w, uint64_t* counts, double* w
                   const gs_options* options);
 
 /*
+ * gs_count_3pcf_noalloc - unweighted gs_count_3pcf that allocates nothing.
+ * The paper has no counterpart: this entry point is for callers that may
+ * not let a library allocate memory during a call (a process that gave all
+ * device memory to its own pool, a real-time loop that must avoid the
+ * allocator's locks and synchronisation, code that records its work for
+ * replay and must keep the memory map fixed). Instead of allocating, it
+ * uses one fixed 64 KB scratch array compiled into the library, which every
+ * GPU that loads the library holds until the process exits.
+ *   g       a resident graph (not out-of-core), nb <= 35.
+ *   counts  uint64 [C(nb+2,3)], host or device; identical to gs_count_3pcf.
+ * The first call on each device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's contents:
+ * each call clears what must start at zero, but calls whose device work
+ * overlaps (different streams or host threads) race and give wrong results.
+ * options->kernel_ms, shard and shards are ignored.
+ * Errors: GS_EINVAL (NULL, out-of-core graph), GS_ERANGE (nb > 35, or more
+ * than 64 devices), GS_ETIMEOUT, GS_ECUDA.
+ */
+int gs_count_3pcf_noalloc(const gs_graph* g, uint64_t* counts, const gs_options* options);
+
+/*
  * gs_count_3pcf_batch - gs_count_3pcf for many catalogues in one
  * persistent launch: the hubs of all graphs form one work queue, so small
  * catalogues share the GPU instead of each paying a launch and a tail.

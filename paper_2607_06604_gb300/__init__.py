@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
-    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_3pcf_batch", "gs_count_4pcf",
+    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
 ]
@@ -84,6 +84,7 @@ def _load():
         "gs_count_3pcf": ([P, P, P, P, OP], ci),
         "gs_count_4pcf": ([P, P, P, P, OP], ci),
         "gs_count_3pcf_batch": ([P, ctypes.c_int32, P, P, P, OP], ci),
+        "gs_count_3pcf_noalloc": ([P, P, OP], ci),
         "gs_plan_3pcf_batch": ([P, ctypes.c_int32, P, OP, ctypes.POINTER(P)], ci),
         "gs_plan_launch": ([P, P], ci),
         "gs_plan_wait": ([P, P], ci),
@@ -261,6 +262,18 @@ def gs_count_3pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
     _check(_lib.gs_count_3pcf(g.handle, _ptr(w), _ptr(counts), _ptr(wsum), ctypes.byref(o)),
            "gs_count_3pcf")
     return (counts, wsum) if w is not None else counts
+
+
+def gs_count_3pcf_noalloc(g: Graph, counts=None, like=None, **opts):
+    """Unweighted triangle counts through the entry point that allocates no
+    device memory (fixed scratch inside the library; see the C header)."""
+    nc = gs_num_configs(3, g.nb)
+    if counts is None:
+        counts = _empty_like_input(like, (nc,), np.uint64)
+    o = _options(**opts)
+    _check(_lib.gs_count_3pcf_noalloc(g.handle, _ptr(counts), ctypes.byref(o)),
+           "gs_count_3pcf_noalloc")
+    return counts
 
 
 def gs_count_3pcf_batch(graphs, ws=None, like=None, **opts):

@@ -20,6 +20,7 @@
 // atomic per bin. Weighted sums use exact fixed point: 128-bit products in
 // shared 128-bit accumulators, flushed into 192-bit global accumulators.
 #include <algorithm>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -690,6 +691,134 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
 }
 
 }  // namespace gs
+
+// ----------------------------------------------------------------------------
+// Triangle counts without any memory allocation.
+//
+// Some callers cannot let a library allocate device memory during a call:
+// code that runs under a fixed memory plan (a serving process that has
+// handed all of HBM to its own pool), real-time loops that must not hit the
+// allocator's locks or its implicit synchronisation, and code that records
+// its work for later replay and may not change the memory map meanwhile.
+// For them gs_count_3pcf_noalloc counts the triangles of a resident graph
+// using only a fixed scratch array that lives in this library's device
+// image for as long as the library stays loaded (every GPU that loads the
+// library holds it). The array holds the kernel's hub counter and error
+// flag and, when the caller's output is host memory, the counts on their
+// way back, so it limits nb to kNoAllocMaxBins (C(37,3) = 7770 bins).
+//
+// All calls share the one array: calls whose device work overlaps (calls on
+// different streams, or from several host threads, before the earlier ones
+// finished) race on it and give wrong results. Every call clears what must
+// start at zero before its kernel runs.
+namespace gs {
+namespace {
+constexpr int kNoAllocMaxBins = 35;
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+constexpr size_t kNoAllocCountsOffset = 256;  // counter and error flag first
+}  // namespace
+}  // namespace gs
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[gs::kNoAllocScratchBytes];
+
+namespace gs {
+namespace {
+// Device address of g_noalloc_scratch per device. In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per
+// device, with that device current, and passed to the kernel.
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return GS_ERANGE;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return e != cudaSuccess ? cuda_status(e) : GS_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return GS_OK;
+}
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
+                                     const gs_options* options) {
+  using namespace gs;
+  if (!G || !counts) return GS_EINVAL;
+  const Graph& g = G->g;
+  if (!g.d_adj) return GS_EINVAL;  // out-of-core graphs need window buffers
+  if (g.nb > kNoAllocMaxBins) return GS_ERANGE;
+  const Opts o = read_opts(options);
+  cudaStream_t s = o.stream;
+  const int nconf = (int)num_conf3(g.nb);
+  void* scratch = nullptr;
+  int st = noalloc_scratch(&scratch);
+  if (st) return st;
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(base);
+  int* err = reinterpret_cast<int*>(base + 8);
+  const bool dev_out = is_device_ptr(counts);
+  uint64_t* dc = dev_out ? counts : reinterpret_cast<uint64_t*>(base + kNoAllocCountsOffset);
+  cudaError_t e = cudaMemsetAsync(base, 0, 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(uint64_t) * nconf, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (g.n > 0) {
+    Args a;
+    a.one.ptr = g.d_ptr;
+    a.one.deg = g.d_deg;
+    a.one.adj = g.d_adj;
+    a.one.adj_off = 0;
+    a.one.split = g.n;
+    a.one.adj_off2 = 0;
+    a.one.W = nullptr;
+    a.one.counts = reinterpret_cast<unsigned long long*>(dc);
+    a.one.wacc = nullptr;
+    a.one.hub_begin = 0;
+    a.one.hub_end = g.n;
+    a.cats = nullptr;
+    a.base = nullptr;
+    a.ncats = 0;
+    a.nb = g.nb;
+    a.nconf = nconf;
+    a.seg_cap = (o.variant & 1) ? 64 : kSegCap;
+    a.force_hash = (o.variant & 1) ? 1 : 0;
+    a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
+    a.hub_counter = counter;
+    a.err = err;
+    const Count3Launch L = count3_launch(g.nb, nconf, false);
+    a.span_cap = L.span_cap;
+    a.stage_alloc = L.stage_words;
+    a.stage_cap = std::min(a.stage_cap, L.stage_words);
+    void (*kern)(Args) = L.smem_hist ? k_count3<false, true, false> : k_count3<false, false, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.smem);
+    { kern<<<std::max(1, per_sm) * sms, kThreads, L.smem, s>>>(a); note_launch(); }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (!dev_out) {
+    e = cudaMemcpyAsync(counts, dc, sizeof(uint64_t) * nconf, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int herr = 0;
+  e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  return herr ? GS_ETIMEOUT : GS_OK;
+}
 
 // ----------------------------------------------------------------------------
 // Recorded batched launches. A plan uploads the catalogue descriptors once,
