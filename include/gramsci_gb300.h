@@ -54,6 +54,12 @@ enum {
   GS_EUNSUPPORTED = -6  /* weights whose exact weighted sums would not fit */
 };
 
+/* gs_options.flags: accumulate the weighted 3pCF sums exactly (fixed-point
+ * integers, rounded once: identical bits in every execution mode) instead
+ * of in FP64 (the default: per-block FP64 sums, then FP64 atomics; within
+ * about 1e-13 relative of the exact sum, last bits depend on order). */
+#define GS_FLAG_EXACT_WEIGHTS 1u
+
 /* Opaque device-resident neighbour graph, owned by the library. */
 typedef struct gs_graph gs_graph;
 
@@ -72,7 +78,7 @@ typedef struct {
   int32_t variant;
   /* cudaStream_t for all device work; NULL = legacy default stream. */
   void* stream;
-  /* Reserved, must be 0. */
+  /* GS_FLAG_* bits. */
   uint32_t flags;
   /* Hub sharding for multi-GPU splits of one catalogue: with shards > 1 a
    * query counts only the tuples whose smallest internal label lies in the
@@ -154,7 +160,8 @@ int gs_graph_export(const gs_graph* g, int64_t* ptr, int32_t* deg, int32_t* nbr,
  *   w       NULL (unweighted) or float32 [n] weights in caller order.
  *   counts  uint64 [C(nb+2,3)] triangle counts per configuration.
  *   wsum    NULL or float64 [C(nb+2,3)]: sum of w_i w_j w_k per
- *           configuration, accumulated exactly and rounded once.
+ *           configuration, in FP64, or exactly and rounded once with
+ *           GS_FLAG_EXACT_WEIGHTS.
  * Errors: GS_EINVAL, GS_EUNSUPPORTED (weights not finite, or spanning so
  * many binades that the exact sums would not fit), GS_ETIMEOUT, GS_ECUDA.
  */

@@ -150,9 +150,13 @@ def _empty_like_input(ref, shape, np_dtype):
     return np.empty(shape, dtype=np_dtype)
 
 
+GS_FLAG_EXACT_WEIGHTS = 1
+
+
 def _options(stream=None, budget=0, force_windows=0, variant=0, kernel_ms=None, shard=0,
-             shards=0):
+             shards=0, exact=False):
     o = Options()
+    o.flags = GS_FLAG_EXACT_WEIGHTS if exact else 0
     o.shard = int(shard)
     o.shards = int(shards)
     if kernel_ms is not None:  # a ctypes.c_double receiving the kernel time

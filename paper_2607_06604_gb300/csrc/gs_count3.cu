@@ -21,6 +21,7 @@
 // shared 128-bit accumulators, flushed into 192-bit global accumulators.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "gs_internal.cuh"
 
@@ -41,9 +42,11 @@ struct Cat {
   const int32_t* __restrict__ deg;
   const uint32_t* __restrict__ adj;  // row j at row_at(adj, ptr, j, adj_off, split, adj_off2)
   int64_t adj_off, split, adj_off2;
-  const int64_t* __restrict__ W;
+  const int64_t* __restrict__ W;   // exact mode: fixed-point weights
+  const double* __restrict__ Wd;   // FP64 mode: weights
   unsigned long long* counts;  // [nconf]
-  unsigned long long* wacc;    // [nconf][3] 192-bit
+  unsigned long long* wacc;    // exact mode: [nconf][3] 192-bit
+  double* wsd;                 // FP64 mode: [nconf] weighted sums
   int64_t hub_begin, hub_end;
 };
 
@@ -65,21 +68,31 @@ struct Args {
 struct Smem {
   uint8_t* table;      // span_cap bytes; the hash path reuses it as words
   uint32_t* stage;     // stage_alloc words
-  int64_t* wst;        // weighted: stage_alloc staged weights of N+(i)
+  int64_t* wst;        // weighted: stage_alloc staged weights of N+(i) (8 bytes each)
   uint16_t* lut;       // nb^3 configuration indices (or nullptr)
   unsigned* hist;      // nconf
-  unsigned long long* whist;  // 2 nconf
+  unsigned long long* whist;  // FP64: nconf doubles; exact: 2 nconf (lo, hi) words
 };
 
 __device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int nb) {
   return sm.lut ? (int)sm.lut[(bij * nb + bik) * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
 }
 
-template <bool WEIGHTED, bool SMEM_HIST>
-__device__ inline void record(const Smem& sm, const Cat& c, int cf, int64_t Wij, int64_t Wk) {
+// Weight modes: kNone, kFp64 (w_i w_j w_k in FP64, per-CTA shared FP64
+// sums, one reduction per triangle) and kExact (fixed-point integers: exact
+// 128-bit products in shared 128-bit accumulators, 192-bit global sums).
+enum : int { kNone = 0, kFp64 = 1, kExact = 2 };
+template <int WM>
+using WType = typename std::conditional<WM == kFp64, double, int64_t>::type;
+
+template <int WM, bool SMEM_HIST>
+__device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Wij, WType<WM> Wk) {
   if (SMEM_HIST) atomicAdd(sm.hist + cf, 1u);
   else atomicAdd(c.counts + cf, 1ull);
-  if (WEIGHTED) {
+  if constexpr (WM == kFp64) {
+    if (SMEM_HIST) atomicAdd(reinterpret_cast<double*>(sm.whist) + cf, Wij * Wk);
+    else atomicAdd(c.wsd + cf, Wij * Wk);
+  } else if constexpr (WM == kExact) {
     long long lo, hi;
     mul_i128(Wij, Wk, &lo, &hi);
     if (SMEM_HIST) atomic_add_i128(sm.whist + 2 * cf, lo, hi);
@@ -87,8 +100,17 @@ __device__ inline void record(const Smem& sm, const Cat& c, int cf, int64_t Wij,
   }
 }
 
-template <bool WEIGHTED, bool SMEM_HIST, bool BATCH>
+template <int WM>
+__device__ inline WType<WM> wget(const Cat& c, int64_t k) {
+  if constexpr (WM == kFp64) return c.Wd[k];
+  else if constexpr (WM == kExact) return c.W[k];
+  else return 0;
+}
+
+template <int WM, bool SMEM_HIST, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
+  constexpr bool WEIGHTED = WM != kNone;
+  using WT = WType<WM>;
   extern __shared__ __align__(16) unsigned char smem[];
   Smem sm;
   {
@@ -123,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   if (SMEM_HIST) {
     for (int k = tid; k < a.nconf; k += kThreads) sm.hist[k] = 0;
     if (WEIGHTED)
-      for (int k = tid; k < 2 * a.nconf; k += kThreads) sm.whist[k] = 0;
+      for (int k = tid; k < (WM == kExact ? 2 : 1) * a.nconf; k += kThreads) sm.whist[k] = 0;
   }
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -144,7 +166,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         atomicAdd(c.counts + k, (unsigned long long)v);
         sm.hist[k] = 0;
       }
-      if (WEIGHTED) {
+      if (WM == kFp64) {
+        double* wh = reinterpret_cast<double*>(sm.whist);
+        if (wh[k] != 0.0) {
+          atomicAdd(c.wsd + k, wh[k]);
+          wh[k] = 0.0;
+        }
+      } else if (WM == kExact) {
         const unsigned long long lo = sm.whist[2 * k], hi = sm.whist[2 * k + 1];
         if (lo | hi) {
           atomic_add_i192(c.wacc + 3 * k, lo, hi);
@@ -220,7 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       continue;
     }
     const uint32_t* row = row_at(c.adj, c.ptr, i, c.adj_off, c.split, c.adj_off2);
-    const int64_t Wi = WEIGHTED ? c.W[i] : 0;
+    const WT Wi = wget<WM>(c, i);
+    WT* wst = reinterpret_cast<WT*>(sm.wst);
     const uint32_t hub_hi = edge_id(row[d - 1]);
     const int64_t span = (int64_t)hub_hi - i;  // ids i+1 .. hub_hi
     const bool staged = d <= a.stage_cap;
@@ -232,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       if (staged) {
         if (tid == 0) bulk_load(sm.stage, row, (uint32_t)pad_row(d) * 4u, &bar);
         if (WEIGHTED)
-          for (int k = tid; k < d; k += kThreads) sm.wst[k] = c.W[edge_id(row[k])];
+          for (int k = tid; k < d; k += kThreads) wst[k] = wget<WM>(c, edge_id(row[k]));
         if (!wait_stage()) return;
       }
       const uint32_t* hr = staged ? sm.stage : row;
@@ -294,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
         for (;;) {
           const int bij = (int)edge_bin(wij);
-          const int64_t Wij = WEIGHTED ? Wi * (staged ? sm.wst[sp] : c.W[edge_id(wij)]) : 0;
+          const WT Wij = Wi * (staged ? wst[sp] : wget<WM>(c, edge_id(wij)));
           const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
           const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
           uint4 vn = none;
@@ -326,15 +355,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               const uint32_t bit = 1u << (off & 31);
               if (bw & bit) {
                 const int pos = (int)pre[off >> 5] + __popc(bw & (bit - 1u));
-                record<WEIGHTED, SMEM_HIST>(
+                record<WM, SMEM_HIST>(
                     sm, c, conf_index(sm, bij, (int)edge_bin(hr[pos]), (int)edge_bin(vv[q]), nb),
-                    Wij, sm.wst[pos]);
+                    Wij, wst[pos]);
               }
             } else {
               const uint8_t bik = sm.table[off];
               if (bik != kAbsent)
-                record<WEIGHTED, SMEM_HIST>(sm, c, conf_index(sm, bij, bik, (int)edge_bin(vv[q]), nb),
-                                            0, 0);
+                record<WM, SMEM_HIST>(sm, c, conf_index(sm, bij, bik, (int)edge_bin(vv[q]), nb),
+                                      WT(0), WT(0));
             }
           }
           if (more) {
@@ -393,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         const uint32_t j = edge_id(wij);
         if (j >= seg_hi) break;  // every k > j; none left in this segment
         const int bij = (int)edge_bin(wij);
-        const int64_t Wij = WEIGHTED ? Wi * c.W[j] : 0;
+        const WT Wij = Wi * wget<WM>(c, j);
         const uint32_t* rj = row_at(c.adj, c.ptr, j, c.adj_off, c.split, c.adj_off2);
         const int dj4 = (int)pad_row(c.deg[j]);
         int start = 0;
@@ -421,9 +450,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               const uint32_t e = table[h];
               if (e == kSentinel) break;
               if (edge_id(e) == key) {
-                record<WEIGHTED, SMEM_HIST>(
+                record<WM, SMEM_HIST>(
                     sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wij,
-                    WEIGHTED ? c.W[key] : 0);
+                    wget<WM>(c, key));
                 break;
               }
               h = (h + 1) & (T - 1);
@@ -453,7 +482,8 @@ struct Count3Launch {
   bool smem_hist = true;
 };
 
-Count3Launch count3_launch(int nb, int nconf, bool weighted) {
+Count3Launch count3_launch(int nb, int nconf, int wmode) {
+  const bool weighted = wmode != kNone;
   // weighted launches stage rows and weights of up to 2048 neighbours
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -461,7 +491,7 @@ Count3Launch count3_launch(int nb, int nconf, bool weighted) {
   auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   const size_t nb3 = (size_t)nb * nb * nb;
   const size_t lut = nb3 <= (size_t)kLutMax ? pad16(nb3 * 2) : 0;
-  size_t hist = pad16((size_t)nconf * 4) + (weighted ? (size_t)nconf * 16 : 0);
+  size_t hist = pad16((size_t)nconf * 4) + (size_t)nconf * (wmode == kExact ? 16 : wmode == kFp64 ? 8 : 0);
   Count3Launch L;
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
   const size_t stage_words = weighted ? 2048 : kStageCap;
@@ -547,28 +577,32 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.one.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.one.W = fw ? fw->d_W : nullptr;
-  const bool weighted = fw && d_wsum;
-  a.one.wacc = weighted ? sc.alloc<unsigned long long>(3 * (size_t)nconf) : nullptr;
+  a.one.Wd = fw ? fw->d_Wd : nullptr;
+  const int wm = (fw && d_wsum) ? (o.exact_weights ? kExact : kFp64) : kNone;
+  a.one.wacc = wm == kExact ? sc.alloc<unsigned long long>(3 * (size_t)nconf) : nullptr;
+  a.one.wsd = wm == kFp64 ? d_wsum : nullptr;
   a.hub_counter = sc.alloc<unsigned long long>(1);
   a.err = sc.alloc<int>(1);
-  if (!a.hub_counter || !a.err || (weighted && !a.one.wacc)) return GS_ENOMEM;
+  if (!a.hub_counter || !a.err || (wm == kExact && !a.one.wacc)) return GS_ENOMEM;
   cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * nconf, s);
-  if (weighted) cudaMemsetAsync(a.one.wacc, 0, sizeof(unsigned long long) * 3 * nconf, s);
+  if (wm == kExact) cudaMemsetAsync(a.one.wacc, 0, sizeof(unsigned long long) * 3 * nconf, s);
+  if (wm == kFp64) cudaMemsetAsync(d_wsum, 0, sizeof(double) * nconf, s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   if (g.n == 0) {
     if (d_wsum) cudaMemsetAsync(d_wsum, 0, sizeof(double) * nconf, s);
     return cuda_status(cudaGetLastError());
   }
 
-  const Count3Launch L = count3_launch(g.nb, nconf, weighted);
+  const Count3Launch L = count3_launch(g.nb, nconf, wm);
   a.span_cap = L.span_cap;
   a.stage_alloc = L.stage_words;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
-  if (weighted) kern = smem_hist ? k_count3<true, true, false> : k_count3<true, false, false>;
-  else kern = smem_hist ? k_count3<false, true, false> : k_count3<false, false, false>;
+  if (wm == kExact) kern = smem_hist ? k_count3<kExact, true, false> : k_count3<kExact, false, false>;
+  else if (wm == kFp64) kern = smem_hist ? k_count3<kFp64, true, false> : k_count3<kFp64, false, false>;
+  else kern = smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -592,9 +626,9 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   if (st) return st;
   cudaError_t e;
   if (d_wsum) {
-    if (weighted)
+    if (wm == kExact)
       { k_i192_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(a.one.wacc, nconf, 3 * fw->scale, d_wsum); note_launch(); }
-    else
+    else if (wm == kNone)
       { k_u64_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(a.one.counts, nconf, d_wsum); note_launch(); }
   }
   int herr = 0;
@@ -610,12 +644,12 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaStream_t s = o.stream;
   const int nb = gr[0]->nb;
   const int nconf = (int)num_conf3(nb);
-  const bool weighted = fws != nullptr && d_wsum != nullptr;
+  const int wm = (fws && d_wsum) ? (o.exact_weights ? kExact : kFp64) : kNone;
   std::vector<Cat> cats(ng);
   std::vector<int64_t> base(ng + 1, 0);
   unsigned long long* wacc =
-      weighted ? sc.alloc<unsigned long long>(3 * (size_t)nconf * ng) : nullptr;
-  if (weighted && !wacc) return GS_ENOMEM;
+      wm == kExact ? sc.alloc<unsigned long long>(3 * (size_t)nconf * ng) : nullptr;
+  if (wm == kExact && !wacc) return GS_ENOMEM;
   for (int k = 0; k < ng; ++k) {
     const Graph& g = *gr[k];
     Cat& c = cats[k];
@@ -625,15 +659,22 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
     c.adj_off = 0;
     c.split = g.n;
     c.adj_off2 = 0;
-    c.W = weighted ? fws[k].d_W : nullptr;
+    c.W = fws ? fws[k].d_W : nullptr;
+    c.Wd = fws ? fws[k].d_Wd : nullptr;
     c.counts = reinterpret_cast<unsigned long long*>(d_counts[k]);
-    c.wacc = weighted ? wacc + 3 * (size_t)nconf * k : nullptr;
+    c.wacc = wm == kExact ? wacc + 3 * (size_t)nconf * k : nullptr;
+    c.wsd = nullptr;
+    if (wm == kFp64) {  // a catalogue without a wsum output still needs somewhere to add
+      c.wsd = d_wsum[k] ? d_wsum[k] : sc.alloc<double>(nconf);
+      if (!c.wsd) return GS_ENOMEM;
+      cudaMemsetAsync(c.wsd, 0, sizeof(double) * nconf, s);
+    }
     c.hub_begin = 0;
     c.hub_end = g.n;
     base[k + 1] = base[k] + g.n;
     cudaMemsetAsync(d_counts[k], 0, sizeof(uint64_t) * nconf, s);
   }
-  if (weighted) cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * 3 * nconf * ng, s);
+  if (wm == kExact) cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * 3 * nconf * ng, s);
   Cat* d_cats = sc.alloc<Cat>(ng);
   int64_t* d_base = sc.alloc<int64_t>(ng + 1);
   Args a;
@@ -653,15 +694,16 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
-  const Count3Launch L = count3_launch(nb, nconf, weighted);
+  const Count3Launch L = count3_launch(nb, nconf, wm);
   a.span_cap = L.span_cap;
   a.stage_alloc = L.stage_words;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
-  if (weighted) kern = smem_hist ? k_count3<true, true, true> : k_count3<true, false, true>;
-  else kern = smem_hist ? k_count3<false, true, true> : k_count3<false, false, true>;
+  if (wm == kExact) kern = smem_hist ? k_count3<kExact, true, true> : k_count3<kExact, false, true>;
+  else if (wm == kFp64) kern = smem_hist ? k_count3<kFp64, true, true> : k_count3<kFp64, false, true>;
+  else kern = smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -675,10 +717,10 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   if (e != cudaSuccess) return cuda_status(e);
   for (int k = 0; k < ng; ++k) {
     if (!d_wsum || !d_wsum[k]) continue;
-    if (weighted)
+    if (wm == kExact)
       { k_i192_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(wacc + 3 * (size_t)nconf * k, nconf,
                                                            3 * fws[k].scale, d_wsum[k]); note_launch(); }
-    else
+    else if (wm == kNone)
       { k_u64_to_double<<<(nconf + 255) / 256, 256, 0, s>>>(
           reinterpret_cast<const unsigned long long*>(d_counts[k]), nconf, d_wsum[k]); note_launch(); }
   }
@@ -781,8 +823,10 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.one.split = g.n;
     a.one.adj_off2 = 0;
     a.one.W = nullptr;
+    a.one.Wd = nullptr;
     a.one.counts = reinterpret_cast<unsigned long long*>(dc);
     a.one.wacc = nullptr;
+    a.one.wsd = nullptr;
     a.one.hub_begin = 0;
     a.one.hub_end = g.n;
     a.cats = nullptr;
@@ -795,11 +839,11 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
     a.hub_counter = counter;
     a.err = err;
-    const Count3Launch L = count3_launch(g.nb, nconf, false);
+    const Count3Launch L = count3_launch(g.nb, nconf, kNone);
     a.span_cap = L.span_cap;
     a.stage_alloc = L.stage_words;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
-    void (*kern)(Args) = L.smem_hist ? k_count3<false, true, false> : k_count3<false, false, false>;
+    void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -862,8 +906,10 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
     c.split = g.n;
     c.adj_off2 = 0;
     c.W = nullptr;
+    c.Wd = nullptr;
     c.counts = reinterpret_cast<unsigned long long*>(counts[k]);
     c.wacc = nullptr;
+    c.wsd = nullptr;
     c.hub_begin = 0;
     c.hub_end = g.n;
     base[k + 1] = base[k] + g.n;
@@ -889,11 +935,11 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.hub_counter = P->counter;
   a.err = P->err;
-  const Count3Launch L = count3_launch(nb, nconf, false);
+  const Count3Launch L = count3_launch(nb, nconf, kNone);
   a.span_cap = L.span_cap;
   a.stage_alloc = L.stage_words;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
-  void (*kern)(Args) = L.smem_hist ? k_count3<false, true, true> : k_count3<false, false, true>;
+  void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
   int per_sm = 0, sms = 0, dev = 0;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
   cudaGetDevice(&dev);

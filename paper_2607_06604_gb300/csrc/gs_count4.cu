@@ -22,6 +22,7 @@
 // 64-bit atomics. Hubs with more than kMaxSmemRow neighbours run in a
 // second launch whose per-hub workspace lives in global scratch.
 #include <algorithm>
+#include <type_traits>
 
 #include "gs_internal.cuh"
 
@@ -38,13 +39,16 @@ struct Args {
   const uint32_t* __restrict__ adj;  // row i at row_at(adj, ptr, i, adj_off, split, adj_off2)
   int64_t adj_off, split, adj_off2;
   int64_t hub_begin, hub_end;
+  const int64_t* __restrict__ big;  // hubs above the shared capacity, taken first
+  int64_t nbig;
   const int4* __restrict__ xyzp;
   const int64_t* __restrict__ e2g;
   const uint32_t* __restrict__ lut;
   int64_t n, box;
   int nb, n_orbits;
-  int row_lo, row_hi;  // this launch handles hubs with row_lo <= deg <= row_hi
-  int mcap;            // workspace capacity (words)
+  int mcap;   // shared-memory workspace capacity (neighbours)
+  int thr;    // hubs with more neighbours than this use the global workspace
+  int gcap;   // global workspace capacity (neighbours)
   unsigned long long* even;
   unsigned long long* odd;
   unsigned long long* weven;  // [n_orbits][3] 192-bit
@@ -52,7 +56,7 @@ struct Args {
   const int64_t* __restrict__ W;
   unsigned long long* hub_counter;
   int* err;
-  unsigned char* gscratch;  // BIG: per-CTA workspace
+  unsigned char* gscratch;  // per-CTA global workspace
   size_t gscratch_stride;
 };
 
@@ -64,7 +68,9 @@ __device__ inline int64_t mi(int64_t d, int64_t box) {
   return d;
 }
 
-__device__ inline int bin_of(int64_t D2, const int64_t* e2, int nb) {
+// Largest b with e2[b] <= D2 (the caller knows D2 is an edge).
+template <class T>
+__device__ inline int bin_of(T D2, const T* e2, int nb) {
   int lo = 0, hi = nb;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -74,58 +80,266 @@ __device__ inline int bin_of(int64_t D2, const int64_t* e2, int nb) {
   return lo;
 }
 
-__device__ inline int64_t d2(const int4& p, const int4& q) {
-  const int64_t x = (int64_t)q.x - p.x, y = (int64_t)q.y - p.y, z = (int64_t)q.z - p.z;
-  return x * x + y * y + z * z;
+// Squared distance between two hub-relative displacements. With
+// SMALLR (E_nb < 2^15) every component of an edge is below 2^15 and the sum
+// below 2^32, so 32-bit arithmetic is exact.
+template <bool SMALLR>
+__device__ inline auto d2(const int4& p, const int4& q) {
+  if constexpr (SMALLR) {
+    const int x = q.x - p.x, y = q.y - p.y, z = q.z - p.z;
+    return (uint32_t)(x * x) + (uint32_t)(y * y) + (uint32_t)(z * z);
+  } else {
+    const int64_t x = (int64_t)q.x - p.x, y = (int64_t)q.y - p.y, z = (int64_t)q.z - p.z;
+    return x * x + y * y + z * z;
+  }
+}
+
+// det[da, db, dc] exactly. With SMALLR the 2x2 minors fit in 32 bits.
+template <bool SMALLR>
+__device__ inline int64_t det3(const int4& da, const int4& db, const int4& dc) {
+  if constexpr (SMALLR) {
+    const int m0 = db.y * dc.z - db.z * dc.y;
+    const int m1 = db.x * dc.z - db.z * dc.x;
+    const int m2 = db.x * dc.y - db.y * dc.x;
+    return (int64_t)da.x * m0 - (int64_t)da.y * m1 + (int64_t)da.z * m2;
+  } else {
+    return (int64_t)da.x * ((int64_t)db.y * dc.z - (int64_t)db.z * dc.y) -
+           (int64_t)da.y * ((int64_t)db.x * dc.z - (int64_t)db.z * dc.x) +
+           (int64_t)da.z * ((int64_t)db.x * dc.y - (int64_t)db.y * dc.x);
+  }
 }
 
 struct Workspace {
-  uint32_t* row;      // staged N+(i) words (m4)
+  uint32_t* row;      // staged N+(i) words
   int4* disp;         // displacement of each neighbour from the hub
   unsigned long long* table;  // hash: (id << 32) | local index, empty = ~0
   uint32_t* bits;     // m x W bit matrix
   uint32_t* queue;    // per-warp (b, c) queue: kWarps x 64 words, then kWarps x 64 bytes
 };
 
-template <bool PARITY, bool WEIGHTED, bool BIG>
+__device__ inline Workspace carve(unsigned char* p, int cap) {
+  int tbits = 5;
+  while ((1 << tbits) < 2 * cap) ++tbits;
+  const int Wc = (cap + 31) / 32;
+  Workspace w;
+  w.row = reinterpret_cast<uint32_t*>(p);
+  p += (size_t)pad_row(cap) * 4;
+  w.disp = reinterpret_cast<int4*>(p);
+  p += (size_t)cap * 16;
+  w.table = reinterpret_cast<unsigned long long*>(p);
+  p += (size_t)(1 << tbits) * 8;
+  w.bits = reinterpret_cast<uint32_t*>(p);
+  p += (size_t)cap * Wc * 4;
+  w.queue = reinterpret_cast<uint32_t*>(p);
+  return w;
+}
+
+// One hub: stage N+(i), build the neighbour bit matrix, enumerate the
+// tetrahedra. GW: the workspace is in global memory (rows above the shared
+// capacity) and counts go straight to the global histograms. Returns false
+// when the staging copy timed out.
+template <bool PARITY, bool WEIGHTED, bool SMALLR, bool GW, class E2T>
+__device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned* h_even,
+                     int* h_odd, int64_t i, int m, uint64_t* bar, uint32_t& phase) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = a.nb;
+  const int W = (m + 31) / 32;
+  const uint32_t* grow = row_at(a.adj, a.ptr, i, a.adj_off, a.split, a.adj_off2);
+  const uint32_t* row = w.row;
+  if (!GW) {
+    if (tid == 0) bulk_load(w.row, grow, (uint32_t)pad_row(m) * 4u, bar);
+  } else {
+    row = grow;
+  }
+  int tbits = 5;
+  while ((1 << tbits) < 2 * m) ++tbits;
+  const int T = 1 << tbits, shift = 32 - tbits;
+  for (int k = tid; k < T; k += kThreads) w.table[k] = ~0ull;
+  for (int k = tid; k < m * W; k += kThreads) w.bits[k] = 0u;
+  if (!GW) {
+    const bool ok = mbar_wait(bar, phase, kWaitLimit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(a.err, kErrTimeout);
+      return false;
+    }
+  } else {
+    __syncthreads();
+  }
+  const int4 P = a.xyzp[i];
+  for (int k = tid; k < m; k += kThreads) {
+    const uint32_t id = edge_id(row[k]);
+    const int4 Q = a.xyzp[id];
+    w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
+                          (int)mi((int64_t)Q.z - P.z, a.box), 0);
+    uint32_t h = (id * kHashMul) >> shift;
+    const unsigned long long ent = ((unsigned long long)id << 32) | (unsigned)k;
+    while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
+  }
+  __syncthreads();
+  // bit matrix: row a gets bit c for every c > a adjacent to j_a
+  const uint32_t hub_hi = edge_id(row[m - 1]);
+  for (int sa = warp; sa < m - 1; sa += kWarps) {
+    const uint32_t j = edge_id(row[sa]);
+    const uint32_t* rj = row_at(a.adj, a.ptr, j, a.adj_off, a.split, a.adj_off2);
+    const int dj4 = (int)pad_row(a.deg[j]);
+    for (int t0 = 0; t0 < dj4; t0 += 128) {
+      const int t = t0 + lane * 4;
+      const uint4 v = (t < dj4) ? ldg_nc_v4(rj + t)
+                                : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+      const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const uint32_t key = edge_id(vv[qq]);
+        if (key > hub_hi) continue;
+        uint32_t h = (key * kHashMul) >> shift;
+        for (;;) {
+          const unsigned long long e = w.table[h];
+          if (e == ~0ull) break;
+          if ((uint32_t)(e >> 32) == key) {
+            const int c = (int)(e & 0xffffffffu);
+            atomicOr(w.bits + sa * W + (c >> 5), 1u << (c & 31));
+            break;
+          }
+          h = (h + 1) & (T - 1);
+        }
+      }
+      const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+      if (edge_id(last) > hub_hi) break;
+    }
+  }
+  __syncthreads();
+  // tetrahedra: warp per row a, triangles (a, b) in a warp-uniform loop;
+  // the common neighbours c > b of a and b are compacted into a per-warp
+  // queue of (b, c) entries that carries over between triangles, and each
+  // batch of 32 entries is processed one tetrahedron per lane
+  const int64_t Wi = WEIGHTED ? a.W[i] : 0;
+  uint32_t* qbc = w.queue + warp * 64;
+  uint8_t* qb12 = reinterpret_cast<uint8_t*>(w.queue + kWarps * 64) + warp * 64;
+  for (int sa = warp; sa < m - 2; sa += kWarps) {
+    const uint32_t wa = row[sa];
+    const int b01 = (int)edge_bin(wa);
+    const int4 da = w.disp[sa];
+    const int64_t Wia = WEIGHTED ? Wi * a.W[edge_id(wa)] : 0;
+    const uint32_t* bra = w.bits + sa * W;
+    int qn = 0;
+    // process the first 32 queue entries (or all when draining)
+    auto drain = [&](bool all) {
+      while (qn >= 32 || (all && qn > 0)) {
+        const bool active = lane < qn;
+        const uint32_t e = active ? qbc[lane] : 0u;
+        const int b12 = active ? (int)qb12[lane] : 0;
+        __syncwarp();
+        if (active) {
+          const int sb = (int)(e >> 16), sc = (int)(e & 0xFFFFu);
+          const uint32_t wb = row[sb], wcw = row[sc];
+          const int4 db = w.disp[sb], dc = w.disp[sc];
+          const int b02 = (int)edge_bin(wb), b03 = (int)edge_bin(wcw);
+          const int b13 = bin_of(d2<SMALLR>(da, dc), e2, nb);
+          const int b23 = bin_of(d2<SMALLR>(db, dc), e2, nb);
+          const uint32_t ent =
+              a.lut[(((size_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
+          const int orbit = (int)(ent & 0x3FFFFFFFu);
+          if (GW) atomicAdd(a.even + orbit, 1ull);
+          else atomicAdd(h_even + orbit, 1u);
+          long long plo = 0, phi = 0;
+          // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
+          if (WEIGHTED) {
+            mul_i128(Wia, a.W[edge_id(wb)] * a.W[edge_id(wcw)], &plo, &phi);
+            atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
+          }
+          if (PARITY && (ent >> 31)) {
+            const int64_t V = det3<SMALLR>(da, db, dc);
+            if (V != 0) {
+              int sgn = V > 0 ? 1 : -1;
+              if ((ent >> 30) & 1u) sgn = -sgn;
+              if (GW) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
+              else atomicAdd(h_odd + orbit, sgn);
+              if (WEIGHTED) {
+                unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
+                if (sgn < 0) {  // negate the 128-bit product
+                  lo = ~lo + 1ull;
+                  hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+                }
+                atomic_add_i192(a.wodd + 3 * orbit, lo, hi);
+              }
+            }
+          }
+        }
+        if (qn >= 32) {  // keep the overflow (the queue holds at most 63)
+          const int rest = qn - 32;
+          uint32_t mv = 0;
+          uint8_t mb = 0;
+          if (lane < rest) {
+            mv = qbc[32 + lane];
+            mb = qb12[32 + lane];
+          }
+          __syncwarp();
+          if (lane < rest) {
+            qbc[lane] = mv;
+            qb12[lane] = mb;
+          }
+          __syncwarp();
+          qn = rest;
+        } else {
+          qn = 0;
+        }
+      }
+    };
+    for (int wb0 = sa >> 5; wb0 < W; ++wb0) {
+      uint32_t xb = bra[wb0];
+      while (xb) {  // warp-uniform: every lane walks the same bits
+        const int sb = wb0 * 32 + __ffs(xb) - 1;
+        xb &= xb - 1u;
+        const int b12 = bin_of(d2<SMALLR>(da, w.disp[sb]), e2, nb);
+        const uint32_t* brb = w.bits + sb * W;
+        for (int wc = sb >> 5; wc < W; ++wc) {
+          uint32_t x = bra[wc] & brb[wc];
+          if (wc == (sb >> 5)) x &= ~((2u << (sb & 31)) - 1u);
+          if (!x) continue;
+          const bool set = (x >> lane) & 1u;
+          if (set) {
+            const int slot = qn + __popc(x & ((1u << lane) - 1u));
+            qbc[slot] = ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
+            qb12[slot] = (uint8_t)b12;
+          }
+          qn += __popc(x);
+          __syncwarp();
+          drain(false);
+        }
+      }
+    }
+    drain(true);
+  }
+  __syncthreads();
+  return true;
+}
+
+template <bool PARITY, bool WEIGHTED, bool SMALLR>
 __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using E2T = typename std::conditional<SMALLR, uint32_t, int64_t>::type;
   __shared__ uint64_t bar;
   __shared__ int64_t s_hub;
   __shared__ int s_flush;
   __shared__ unsigned long long s_pending;
-  __shared__ int64_t e2[kMaxBins4 + 1];
+  __shared__ E2T e2[kMaxBins4 + 1];
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nb = a.nb;
+  const int tid = threadIdx.x;
   unsigned* h_even = reinterpret_cast<unsigned*>(smem);
   int* h_odd = reinterpret_cast<int*>(h_even + a.n_orbits);
-  unsigned char* ws_base = smem + (size_t)a.n_orbits * 4 * (PARITY ? 2 : 1);
-  ws_base = reinterpret_cast<unsigned char*>(((uintptr_t)ws_base + 15) & ~(uintptr_t)15);
-  if (BIG) ws_base = a.gscratch + (size_t)blockIdx.x * a.gscratch_stride;
-  const int mcap = a.mcap;
-  const int Wcap = (mcap + 31) / 32;
-  int tcap_bits = 5;
-  while ((1 << tcap_bits) < 2 * mcap) ++tcap_bits;
-  Workspace w;
-  {
-    unsigned char* p = ws_base;
-    w.row = reinterpret_cast<uint32_t*>(p);
-    p += (size_t)pad_row(mcap) * 4;
-    w.disp = reinterpret_cast<int4*>(p);
-    p += (size_t)mcap * 16;
-    w.table = reinterpret_cast<unsigned long long*>(p);
-    p += (size_t)(1 << tcap_bits) * 8;
-    w.bits = reinterpret_cast<uint32_t*>(p);
-    p += (size_t)mcap * Wcap * 4;
-    w.queue = reinterpret_cast<uint32_t*>(p);
-  }
+  unsigned char* sws = smem + (size_t)a.n_orbits * 4 * (PARITY ? 2 : 1);
+  sws = reinterpret_cast<unsigned char*>(((uintptr_t)sws + 15) & ~(uintptr_t)15);
+  const Workspace ws_s = carve(sws, a.mcap);
+  const Workspace ws_g = carve(a.gscratch ? a.gscratch + (size_t)blockIdx.x * a.gscratch_stride
+                                          : sws,
+                               a.gscratch ? a.gcap : a.mcap);
 
   for (int k = tid; k < a.n_orbits; k += kThreads) {
     h_even[k] = 0;
     if (PARITY) h_odd[k] = 0;
   }
-  for (int b = tid; b <= nb; b += kThreads) e2[b] = a.e2g[b];
+  for (int b = tid; b <= a.nb; b += kThreads) e2[b] = (E2T)a.e2g[b];
   if (tid == 0) {
     mbar_init(&bar, 1);
     s_pending = 0;
@@ -152,18 +366,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
 
   for (;;) {
     if (tid == 0) {
+      // the long rows first (they are few and slow), then every other hub
+      const int64_t q = (int64_t)atomicAdd(a.hub_counter, 1ull);
       int64_t i;
-      int d;
-      do {  // skip hubs this launch does not handle
-        i = a.hub_begin + (int64_t)atomicAdd(a.hub_counter, 1ull);
-        d = (i < a.hub_end) ? a.deg[i] : 0;
-      } while (i < a.hub_end && (d < 3 || d < a.row_lo || d > a.row_hi));
+      int d = 0;
+      if (q < a.nbig) {
+        i = a.big[q];
+        d = a.deg[i];
+      } else {
+        int64_t qq = q - a.nbig;
+        for (;;) {
+          i = a.hub_begin + qq;
+          d = (i < a.hub_end) ? a.deg[i] : 0;
+          if (i >= a.hub_end || (d >= 3 && d <= a.thr)) break;
+          qq = (int64_t)atomicAdd(a.hub_counter, 1ull) - a.nbig;
+        }
+      }
       s_hub = i;
       s_flush = 0;
-      if (i < a.hub_end) {
+      if (i < a.hub_end && d <= a.thr) {
         const unsigned long long m = (unsigned long long)d;
         const unsigned long long need = m * (m - 1) * (m - 2) / 6;
-        if (!BIG && s_pending + need > 0x7FFFFFFFull) {
+        if (s_pending + need > 0x7FFFFFFFull) {
           s_flush = 1;
           s_pending = need;
         } else {
@@ -179,178 +403,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
       __syncthreads();
     }
     const int m = a.deg[i];
-    const int W = (m + 31) / 32;
-    const uint32_t* grow = row_at(a.adj, a.ptr, i, a.adj_off, a.split, a.adj_off2);
-    const uint32_t* row = w.row;
-    if (!BIG) {
-      if (tid == 0) bulk_load(w.row, grow, (uint32_t)pad_row(m) * 4u, &bar);
-    } else {
-      row = grow;
-    }
-    int tbits = 5;
-    while ((1 << tbits) < 2 * m) ++tbits;
-    const int T = 1 << tbits, shift = 32 - tbits;
-    for (int k = tid; k < T; k += kThreads) w.table[k] = ~0ull;
-    for (int k = tid; k < m * W; k += kThreads) w.bits[k] = 0u;
-    if (!BIG) {
-      const bool ok = mbar_wait(&bar, phase, kWaitLimit);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicOr(a.err, kErrTimeout);
-        return;
-      }
-    } else {
-      __syncthreads();
-    }
-    const int4 P = a.xyzp[i];
-    for (int k = tid; k < m; k += kThreads) {
-      const uint32_t wd = row[k];
-      const uint32_t id = edge_id(wd);
-      const int4 Q = a.xyzp[id];
-      w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
-                            (int)mi((int64_t)Q.z - P.z, a.box), 0);
-      uint32_t h = (id * kHashMul) >> shift;
-      const unsigned long long ent = ((unsigned long long)id << 32) | (unsigned)k;
-      while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
-    }
-    __syncthreads();
-    // bit matrix: row a gets bit c for every c > a adjacent to j_a
-    const uint32_t hub_hi = edge_id(row[m - 1]);
-    for (int sa = warp; sa < m - 1; sa += kWarps) {
-      const uint32_t j = edge_id(row[sa]);
-      const uint32_t* rj = row_at(a.adj, a.ptr, j, a.adj_off, a.split, a.adj_off2);
-      const int dj4 = (int)pad_row(a.deg[j]);
-      for (int t0 = 0; t0 < dj4; t0 += 128) {
-        const int t = t0 + lane * 4;
-        const uint4 v = (t < dj4) ? ldg_nc_v4(rj + t)
-                                  : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
-        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          const uint32_t key = edge_id(vv[qq]);
-          if (key > hub_hi) continue;
-          uint32_t h = (key * kHashMul) >> shift;
-          for (;;) {
-            const unsigned long long e = w.table[h];
-            if (e == ~0ull) break;
-            if ((uint32_t)(e >> 32) == key) {
-              const int c = (int)(e & 0xffffffffu);
-              atomicOr(w.bits + sa * W + (c >> 5), 1u << (c & 31));
-              break;
-            }
-            h = (h + 1) & (T - 1);
-          }
-        }
-        const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
-        if (edge_id(last) > hub_hi) break;
-      }
-    }
-    __syncthreads();
-    // tetrahedra: warp per row a, triangles (a, b) in a warp-uniform loop;
-    // the common neighbours c > b of a and b are compacted into a per-warp
-    // queue of (b, c) entries that carries over between triangles, and each
-    // batch of 32 entries is processed one tetrahedron per lane
-    const int64_t Wi = WEIGHTED ? a.W[i] : 0;
-    uint32_t* qbc = w.queue + warp * 64;
-    uint8_t* qb12 = reinterpret_cast<uint8_t*>(w.queue + kWarps * 64) + warp * 64;
-    for (int sa = warp; sa < m - 2; sa += kWarps) {
-      const uint32_t wa = row[sa];
-      const int b01 = (int)edge_bin(wa);
-      const int4 da = w.disp[sa];
-      const int64_t Wia = WEIGHTED ? Wi * a.W[edge_id(wa)] : 0;
-      const uint32_t* bra = w.bits + sa * W;
-      int qn = 0;
-      // process the first 32 queue entries (or all when draining)
-      auto drain = [&](bool all) {
-        while (qn >= 32 || (all && qn > 0)) {
-          const bool active = lane < qn;
-          const uint32_t e = active ? qbc[lane] : 0u;
-          const int b12 = active ? (int)qb12[lane] : 0;
-          __syncwarp();
-          if (active) {
-            const int sb = (int)(e >> 16), sc = (int)(e & 0xFFFFu);
-            const uint32_t wb = row[sb], wcw = row[sc];
-            const int4 db = w.disp[sb], dc = w.disp[sc];
-            const int b02 = (int)edge_bin(wb), b03 = (int)edge_bin(wcw);
-            const int b13 = bin_of(d2(da, dc), e2, nb);
-            const int b23 = bin_of(d2(db, dc), e2, nb);
-            const uint32_t ent =
-                a.lut[(((size_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
-            const int orbit = (int)(ent & 0x3FFFFFFFu);
-            if (BIG) atomicAdd(a.even + orbit, 1ull);
-            else atomicAdd(h_even + orbit, 1u);
-            long long plo = 0, phi = 0;
-            // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
-            if (WEIGHTED) {
-              mul_i128(Wia, a.W[edge_id(wb)] * a.W[edge_id(wcw)], &plo, &phi);
-              atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
-            }
-            if (PARITY && (ent >> 31)) {
-              const int64_t V = (int64_t)da.x * ((int64_t)db.y * dc.z - (int64_t)db.z * dc.y) -
-                                (int64_t)da.y * ((int64_t)db.x * dc.z - (int64_t)db.z * dc.x) +
-                                (int64_t)da.z * ((int64_t)db.x * dc.y - (int64_t)db.y * dc.x);
-              if (V != 0) {
-                int sgn = V > 0 ? 1 : -1;
-                if ((ent >> 30) & 1u) sgn = -sgn;
-                if (BIG) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
-                else atomicAdd(h_odd + orbit, sgn);
-                if (WEIGHTED) {
-                  unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
-                  if (sgn < 0) {  // negate the 128-bit product
-                    lo = ~lo + 1ull;
-                    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
-                  }
-                  atomic_add_i192(a.wodd + 3 * orbit, lo, hi);
-                }
-              }
-            }
-          }
-          if (qn >= 32) {  // keep the overflow (the queue holds at most 63)
-            const int rest = qn - 32;
-            uint32_t mv = 0;
-            uint8_t mb = 0;
-            if (lane < rest) {
-              mv = qbc[32 + lane];
-              mb = qb12[32 + lane];
-            }
-            __syncwarp();
-            if (lane < rest) {
-              qbc[lane] = mv;
-              qb12[lane] = mb;
-            }
-            __syncwarp();
-            qn = rest;
-          } else {
-            qn = 0;
-          }
-        }
-      };
-      for (int wb0 = sa >> 5; wb0 < W; ++wb0) {
-        uint32_t xb = bra[wb0];
-        while (xb) {  // warp-uniform: every lane walks the same bits
-          const int sb = wb0 * 32 + __ffs(xb) - 1;
-          xb &= xb - 1u;
-          const int b12 = bin_of(d2(da, w.disp[sb]), e2, nb);
-          const uint32_t* brb = w.bits + sb * W;
-          for (int wc = sb >> 5; wc < W; ++wc) {
-            uint32_t x = bra[wc] & brb[wc];
-            if (wc == (sb >> 5)) x &= ~((2u << (sb & 31)) - 1u);
-            if (!x) continue;
-            const bool set = (x >> lane) & 1u;
-            if (set) {
-              const int slot = qn + __popc(x & ((1u << lane) - 1u));
-              qbc[slot] = ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
-              qb12[slot] = (uint8_t)b12;
-            }
-            qn += __popc(x);
-            __syncwarp();
-            drain(false);
-          }
-        }
-      }
-      drain(true);
-    }
-    __syncthreads();
+    bool ok;
+    if (m > a.thr)
+      ok = hub4<PARITY, WEIGHTED, SMALLR, true>(a, ws_g, e2, h_even, h_odd, i, m, &bar, phase);
+    else
+      ok = hub4<PARITY, WEIGHTED, SMALLR, false>(a, ws_s, e2, h_even, h_odd, i, m, &bar, phase);
+    if (!ok) return;
   }
   __syncthreads();
   flush();
@@ -389,6 +447,8 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   a.adj_off = 0;
   a.split = g.n;
   a.adj_off2 = 0;
+  a.big = nullptr;
+  a.nbig = 0;
   a.hub_begin = 0;
   a.hub_end = g.n;
   a.xyzp = g.d_xyzp;
@@ -428,32 +488,37 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   while (mcap > 32 && hist_aligned + workspace_bytes(mcap) > (size_t)optin - 1024) mcap -= 32;
   if (hist_aligned + workspace_bytes(mcap) > (size_t)optin - 1024) return GS_ERANGE;
 
-  auto pick = [&](bool big) -> void (*)(Args) {
+  const bool small_r = g.edges[g.nb] < 32768;
+  auto pick = [&]() -> void (*)(Args) {
+#define GS_PICK(P, Wt)                                                       \
+  return small_r ? k_count4<P, Wt, true> : k_count4<P, Wt, false>
     if (parity) {
-      if (weighted) return big ? k_count4<true, true, true> : k_count4<true, true, false>;
-      return big ? k_count4<true, false, true> : k_count4<true, false, false>;
+      if (weighted) GS_PICK(true, true);
+      GS_PICK(true, false);
     }
-    if (weighted) return big ? k_count4<false, true, true> : k_count4<false, true, false>;
-    return big ? k_count4<false, false, true> : k_count4<false, false, false>;
+    if (weighted) GS_PICK(false, true);
+    GS_PICK(false, false);
+#undef GS_PICK
   };
-  // variant 1 sends every hub to the global-workspace launch (exercises it
-  // on any input)
+  // variant 1 sends every hub to the global workspace (exercises it on any
+  // input)
   const bool force_global = (o.variant & 1) != 0;
-  void (*kern_s)(Args) = pick(false);
-  const size_t smem_s = hist_aligned + workspace_bytes(mcap);
-  cudaFuncSetAttribute(kern_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+  const int thr = force_global ? 2 : mcap;
+  void (*kern)(Args) = pick();
+  const size_t smem = hist_aligned + workspace_bytes(mcap);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern_s, kThreads, smem_s);
-  const bool need_big = g.max_deg > mcap || (force_global && g.max_deg >= 3);
-  void (*kern_b)(Args) = pick(true);
-  const size_t smem_b = hist_aligned;
-  size_t stride_b = 0;
-  unsigned char* scratch_b = nullptr;
-  if (need_big) {
-    cudaFuncSetAttribute(kern_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
-    stride_b = (workspace_bytes(g.max_deg) + 255) & ~(size_t)255;
-    scratch_b = sc.alloc<unsigned char>(stride_b * sms);
-    if (!scratch_b) return GS_ENOMEM;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  const int grid = std::max(1, per_sm) * sms;
+  a.mcap = mcap;
+  a.thr = thr;
+  a.gcap = std::max(g.max_deg, 3);
+  a.gscratch = nullptr;
+  a.gscratch_stride = 0;
+  if (g.max_deg > thr) {
+    a.gscratch_stride = (workspace_bytes(a.gcap) + 255) & ~(size_t)255;
+    a.gscratch = sc.alloc<unsigned char>(a.gscratch_stride * grid);
+    if (!a.gscratch) return GS_ENOMEM;
   }
   KernelTimer timer(o.kernel_ms);
   timer.start(s);
@@ -464,34 +529,23 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
     a.adj_off2 = v.off2;
     a.hub_begin = v.h0;
     a.hub_end = v.h1;
-    cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long) * 2, s);
-    // launch 1: rows up to mcap, workspace in shared memory
-    if (!force_global) {
-      Args b = a;
-      b.row_lo = 0;
-      b.row_hi = mcap;
-      b.mcap = mcap;
-      b.gscratch = nullptr;
-      b.gscratch_stride = 0;
-      { kern_s<<<std::max(1, per_sm) * sms, kThreads, smem_s, s>>>(b); note_launch(); }
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_status(e);
+    // the window's long rows go to the front of its hub queue
+    std::vector<int64_t> big;
+    if (g.max_deg > thr)
+      for (int64_t h = v.h0; h < v.h1; ++h)
+        if (g.h_deg[h] > thr) big.push_back(h);
+    a.nbig = (int64_t)big.size();
+    a.big = nullptr;
+    if (!big.empty()) {
+      int64_t* d_big = sc.alloc<int64_t>(big.size());
+      if (!d_big) return GS_ENOMEM;
+      cudaMemcpyAsync(d_big, big.data(), sizeof(int64_t) * big.size(), cudaMemcpyHostToDevice, s);
+      a.big = d_big;
     }
-    // launch 2: longer rows, workspace in global scratch sized from the
-    // longest row of the graph
-    if (need_big) {
-      Args b = a;
-      b.row_lo = force_global ? 0 : mcap + 1;
-      b.row_hi = g.max_deg;
-      b.mcap = g.max_deg;
-      b.gscratch_stride = stride_b;
-      b.gscratch = scratch_b;
-      b.hub_counter = a.hub_counter + 1;
-      { kern_b<<<sms, kThreads, smem_b, s>>>(b); note_launch(); }
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_status(e);
-    }
-    return GS_OK;
+    cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
+    { kern<<<grid, kThreads, smem, s>>>(a); note_launch(); }
+    // the host list must outlive the (pageable, hence synchronous) copy only
+    return cuda_status(cudaGetLastError());
   });
   if (st) return st;
   timer.stop(s);

@@ -460,6 +460,9 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
   g->probe_words = (int64_t)ht[0];
   g->edges_total = (int64_t)ht[1];
   g->max_deg = (int)(ht[2] & 0xffffffffu);
+  g->h_deg.resize(n);
+  ce = cudaMemcpy(g->h_deg.data(), g->d_deg, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+  if (ce != cudaSuccess) return cuda_status(ce);
   timer.publish();
   return cuda_status(cudaGetLastError());
 }

@@ -61,6 +61,7 @@ struct Graph {
   uint32_t* d_adj = nullptr;    // [slots] packed edge words (resident graphs)
   uint32_t* h_adj = nullptr;    // [slots] pinned host copy (out-of-core graphs)
   std::vector<int64_t> h_ptr;   // host copy of d_ptr (window planning)
+  std::vector<int32_t> h_deg;   // host copy of d_deg
   // out-of-core planning. In a periodic box the ids are x-major, so hubs
   // of the first x-slab have wrap-around neighbours in the last one:
   // wrap_start is the first id of the last x-slab (n for an open box);
@@ -90,6 +91,7 @@ struct Opts {
   cudaStream_t stream = nullptr;
   double* kernel_ms = nullptr;
   int shard = 0, shards = 0;
+  bool exact_weights = false;
 };
 
 // Hub range [lo, hi) of the query's shard (the whole graph when unsharded).
@@ -149,6 +151,7 @@ int64_t num_conf3(int nb);
 // Fixed-point weights: W_i = w_i * 2^scale is an integer for every point.
 struct FixedW {
   int64_t* d_W = nullptr;  // [n], internal order
+  double* d_Wd = nullptr;  // [n], the same weights as doubles
   int scale = 0;
   int bits = 0;  // max bit length of |W_i| plus one sign bit
 };

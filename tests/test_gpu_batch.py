@@ -37,11 +37,16 @@ def test_batch_equals_single_and_oracle(gs):
         c, s = out[k]
         sc, ss = gs.gs_count_3pcf(graphs[k], ws[k])
         assert np.array_equal(c.cpu().numpy(), sc.cpu().numpy())
-        assert np.array_equal(s.cpu().numpy(), ss.cpu().numpy())
+        np.testing.assert_allclose(s.cpu().numpy(), ss.cpu().numpy(), rtol=1e-13)
         if X.shape[0] > 2:
             rc, rw = oracle.Graph(X, box_u, edges).count_3pcf(w)
             assert np.array_equal(c.cpu().numpy(), rc)
             np.testing.assert_allclose(s.cpu().numpy(), rw, rtol=1e-12)
+    # exact weighted sums are identical in and out of a batch
+    out_x = gs.gs_count_3pcf_batch(graphs, ws, exact=True)
+    for k in range(len(sizes)):
+        assert np.array_equal(out_x[k][1].cpu().numpy(),
+                              gs.gs_count_3pcf(graphs[k], ws[k], exact=True)[1].cpu().numpy())
     # unweighted batch, host outputs
     out_u = gs.gs_count_3pcf_batch(graphs)
     for k in range(len(sizes)):

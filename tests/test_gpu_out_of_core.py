@@ -36,7 +36,8 @@ def resident(gs, case):
     X, box_u, edges, w = case
     g = gs.gs_build_graph(X, box_u, edges)
     assert gs.gs_graph_info(g)["windows"] == 1
-    out = {"c3": gs.gs_count_3pcf(g, w), "c4": gs.gs_count_4pcf_parity(g),
+    out = {"c3": gs.gs_count_3pcf(g, w, exact=True), "c3f": gs.gs_count_3pcf(g, w),
+           "c4": gs.gs_count_4pcf_parity(g),
            "pairs": gs.gs_disconnected_4pcf(g, w), "export": gs.gs_graph_export(g),
            "info": gs.gs_graph_info(g)}
     # the resident path itself is pinned to the oracle
@@ -53,9 +54,11 @@ def test_forced_windows_bit_identical(gs, case, resident, windows):
     g = gs.gs_build_graph(X, box_u, edges, force_windows=windows)
     info = gs.gs_graph_info(g)
     assert info["windows"] == windows or (windows > 1 and info["windows"] > 1)
-    c, ws = gs.gs_count_3pcf(g, w)
+    c, ws = gs.gs_count_3pcf(g, w, exact=True)
     assert np.array_equal(c, resident["c3"][0])
     assert np.array_equal(ws, resident["c3"][1])  # exact sums: bit-identical
+    _, wf = gs.gs_count_3pcf(g, w)
+    np.testing.assert_allclose(wf, resident["c3f"][1], rtol=1e-13)
     e, o = gs.gs_count_4pcf_parity(g)
     assert np.array_equal(e, resident["c4"][0]) and np.array_equal(o, resident["c4"][1])
     p, xi, z = gs.gs_disconnected_4pcf(g, w)
@@ -77,7 +80,7 @@ def test_budget_driven_windows(gs, case, resident):
     g = gs.gs_build_graph(X, box_u, edges, budget=budget)
     info = gs.gs_graph_info(g)
     assert info["windows"] >= 2
-    c, ws = gs.gs_count_3pcf(g, w)
+    c, ws = gs.gs_count_3pcf(g, w, exact=True)
     assert np.array_equal(c, resident["c3"][0]) and np.array_equal(ws, resident["c3"][1])
     # a query may ask for smaller windows than the build did
     c2 = gs.gs_count_3pcf(g, budget=int(budget * 0.75))
@@ -116,4 +119,4 @@ def test_hub_shards_sum_exactly(gs, case, resident, shards, windows):
     assert np.array_equal(o, resident["c4"][1])
     assert np.array_equal(p, resident["pairs"][0].astype(np.int64))
     ws = sum(gs.gs_count_3pcf(g, w, shard=k, shards=shards)[1] for k in range(shards))
-    np.testing.assert_allclose(ws, resident["c3"][1], rtol=1e-14)
+    np.testing.assert_allclose(ws, resident["c3"][1], rtol=1e-13)

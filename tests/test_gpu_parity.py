@@ -173,10 +173,15 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     # every kernel path gives the same answer: hash path in 64-word segments
     # (variant 1) and the table path reading hub rows from global (variant 2)
     g = gs.gs_build_graph(X, bu, edges)
+    ex_c, ex_w = gs.gs_count_3pcf(g, w, exact=True)
+    assert np.array_equal(ex_c, rc)
+    np.testing.assert_allclose(ex_w, rw, rtol=RTOL)
     for variant in (1, 2):
         vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(vc, rc), variant
-        assert np.array_equal(vw, gw), variant
+        np.testing.assert_allclose(vw, gw, rtol=1e-13)
+        # exact sums are identical bit for bit whichever path found them
+        assert np.array_equal(gs.gs_count_3pcf(g, w, variant=variant, exact=True)[1], ex_w)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
@@ -216,6 +221,8 @@ def test_3pcf_long_rows_segmented(gs, torch_mod, periodic):
     gc, gw = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1)
     assert np.array_equal(gc.cpu().numpy(), rc)
     np.testing.assert_allclose(gw.cpu().numpy(), rw, rtol=RTOL)
+    _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1, exact=True)
+    np.testing.assert_allclose(gx.cpu().numpy(), rw, rtol=RTOL)
 
 
 def test_3pcf_host_and_device_pointers(gs, torch_mod):
@@ -360,6 +367,9 @@ def test_full_size_ddd_bit_exact(gs, torch_mod, ns1m):
     assert rc.sum() > 1e9
     assert np.array_equal(gc, rc)
     np.testing.assert_allclose(gw, rw, rtol=RTOL)
+    g = gs.gs_build_graph(dev(torch_mod, X), s["box_u"], s["edges_u"])
+    _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w), exact=True)
+    np.testing.assert_allclose(gx.cpu().numpy(), rw, rtol=RTOL)
 
 
 def test_full_size_rrr_properties(gs, torch_mod):
