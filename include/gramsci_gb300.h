@@ -54,12 +54,6 @@ enum {
   GS_EUNSUPPORTED = -6  /* weights whose exact weighted sums would not fit */
 };
 
-/* gs_options.flags: accumulate the weighted 3pCF sums exactly (fixed-point
- * integers, rounded once: identical bits in every execution mode) instead
- * of in FP64 (the default: per-block FP64 sums, then FP64 atomics; within
- * about 1e-13 relative of the exact sum, last bits depend on order). */
-#define GS_FLAG_EXACT_WEIGHTS 1u
-
 /* Opaque device-resident neighbour graph, owned by the library. */
 typedef struct gs_graph gs_graph;
 
@@ -71,14 +65,17 @@ typedef struct {
   /* > 0 forces that many row windows (out-of-core mode even when the
    * graph fits); 0 = automatic. */
   int32_t force_windows;
-  /* Kernel variant: 0 = automatic. 1 = exercise the long-row code paths
-   * on any input (gs_count_3pcf stages hub rows in 64-word segments;
-   * gs_count_4pcf* keeps every hub's workspace in global memory). Results
-   * are identical; variant 1 is slower and meant for testing. */
+  /* Kernel variant bits: 0 = automatic. 1 = exercise the long-row code
+   * paths on any input (gs_count_3pcf probes a hash of the hub row staged
+   * in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
+   * global memory). 2 = gs_count_3pcf reads hub rows from global memory
+   * instead of staging them. 4 = gs_count_3pcf looks configuration indices
+   * up in a shared table instead of computing them. Results are identical;
+   * the bits exist for testing and tuning. */
   int32_t variant;
   /* cudaStream_t for all device work; NULL = legacy default stream. */
   void* stream;
-  /* GS_FLAG_* bits. */
+  /* Reserved, must be 0. */
   uint32_t flags;
   /* Hub sharding for multi-GPU splits of one catalogue: with shards > 1 a
    * query counts only the tuples whose smallest internal label lies in the
@@ -160,13 +157,24 @@ int gs_graph_export(const gs_graph* g, int64_t* ptr, int32_t* deg, int32_t* nbr,
  *   w       NULL (unweighted) or float32 [n] weights in caller order.
  *   counts  uint64 [C(nb+2,3)] triangle counts per configuration.
  *   wsum    NULL or float64 [C(nb+2,3)]: sum of w_i w_j w_k per
- *           configuration, in FP64, or exactly and rounded once with
- *           GS_FLAG_EXACT_WEIGHTS.
+ *           configuration, accumulated exactly and rounded once.
  * Errors: GS_EINVAL, GS_EUNSUPPORTED (weights not finite, or spanning so
  * many binades that the exact sums would not fit), GS_ETIMEOUT, GS_ECUDA.
  */
 int gs_count_3pcf(const gs_graph* g, const float* w, uint64_t* counts, double* wsum,
                   const gs_options* options);
+
+/*
+ * gs_tune_3pcf - autotuner for gs_count_3pcf. Times the launch variants
+ * (hub rows staged in shared memory or read from global memory;
+ * configuration indices computed or looked up) on one hub shard of g
+ * (about 1/16 of its edges, weighted like w) and remembers the fastest for
+ * graphs with the same nb, weight mode and degree class; calls with
+ * options->variant = -1 then use it (0 when nothing was tuned).
+ * *best_variant receives the choice. Errors: as gs_count_3pcf.
+ */
+int gs_tune_3pcf(const gs_graph* g, const float* w, const gs_options* options,
+                 int32_t* best_variant);
 
 /*
  * gs_count_3pcf_noalloc - unweighted gs_count_3pcf that allocates nothing.

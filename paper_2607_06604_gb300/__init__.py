@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
-    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_4pcf",
+    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
 ]
@@ -85,6 +85,7 @@ def _load():
         "gs_count_4pcf": ([P, P, P, P, OP], ci),
         "gs_count_3pcf_batch": ([P, ctypes.c_int32, P, P, P, OP], ci),
         "gs_count_3pcf_noalloc": ([P, P, OP], ci),
+        "gs_tune_3pcf": ([P, P, OP, ctypes.POINTER(ctypes.c_int32)], ci),
         "gs_plan_3pcf_batch": ([P, ctypes.c_int32, P, OP, ctypes.POINTER(P)], ci),
         "gs_plan_launch": ([P, P], ci),
         "gs_plan_wait": ([P, P], ci),
@@ -150,13 +151,9 @@ def _empty_like_input(ref, shape, np_dtype):
     return np.empty(shape, dtype=np_dtype)
 
 
-GS_FLAG_EXACT_WEIGHTS = 1
-
-
 def _options(stream=None, budget=0, force_windows=0, variant=0, kernel_ms=None, shard=0,
-             shards=0, exact=False):
+             shards=0):
     o = Options()
-    o.flags = GS_FLAG_EXACT_WEIGHTS if exact else 0
     o.shard = int(shard)
     o.shards = int(shards)
     if kernel_ms is not None:  # a ctypes.c_double receiving the kernel time
@@ -266,6 +263,15 @@ def gs_count_3pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
     _check(_lib.gs_count_3pcf(g.handle, _ptr(w), _ptr(counts), _ptr(wsum), ctypes.byref(o)),
            "gs_count_3pcf")
     return (counts, wsum) if w is not None else counts
+
+
+def gs_tune_3pcf(g: Graph, w=None, **opts) -> int:
+    """Time the 3pCF launch variants on a sample of g; variant=-1 then uses the best."""
+    best = ctypes.c_int32(0)
+    o = _options(**opts)
+    _check(_lib.gs_tune_3pcf(g.handle, _ptr(w), ctypes.byref(o), ctypes.byref(best)),
+           "gs_tune_3pcf")
+    return int(best.value)
 
 
 def gs_count_3pcf_noalloc(g: Graph, counts=None, like=None, **opts):

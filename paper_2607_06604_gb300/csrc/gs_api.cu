@@ -21,7 +21,6 @@ Opts read_opts(const gs_options* o) {
     r.kernel_ms = o->kernel_ms;
     r.shard = o->shard;
     r.shards = o->shards;
-    r.exact_weights = (o->flags & GS_FLAG_EXACT_WEIGHTS) != 0;
   }
   return r;
 }
@@ -383,12 +382,11 @@ __global__ void k_weight_exponents(const float* w, int64_t n, int* emin, int* em
 }
 
 __global__ void k_weight_fixed(const float* w, const int4* xyzp, int64_t n, int scale,
-                               int64_t* W, double* Wd) {
+                               int64_t* W) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float x = w[xyzp[i].w];
     W[i] = (int64_t)ldexp((double)x, scale);  // exact: x * 2^scale is an integer
-    Wd[i] = (double)x;
   }
 }
 }  // namespace
@@ -397,8 +395,7 @@ int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cu
   const float* dw = static_cast<const float*>(to_device(sc, w, sizeof(float) * g.n, s));
   int* flags = sc.alloc<int>(3);
   int64_t* W = sc.alloc<int64_t>(g.n);
-  double* Wd = sc.alloc<double>(g.n);
-  if (!dw || !flags || !W || !Wd) return GS_ENOMEM;
+  if (!dw || !flags || !W) return GS_ENOMEM;
   const int init[3] = {1 << 20, -(1 << 20), 0};
   cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s);
   { k_weight_exponents<<<304, 256, 0, s>>>(dw, g.n, flags, flags + 1, flags + 2); note_launch(); }
@@ -411,9 +408,8 @@ int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cu
   out->scale = 24 - h[0];
   out->bits = 25 + (h[1] - h[0]) + 1;
   if (out->bits > 31) return GS_EUNSUPPORTED;
-  { k_weight_fixed<<<304, 256, 0, s>>>(dw, g.d_xyzp, g.n, out->scale, W, Wd); note_launch(); }
+  { k_weight_fixed<<<304, 256, 0, s>>>(dw, g.d_xyzp, g.n, out->scale, W); note_launch(); }
   out->d_W = W;
-  out->d_Wd = Wd;
   return cuda_status(cudaGetLastError());
 }
 

@@ -20,7 +20,9 @@
 // atomic per bin. Weighted sums use exact fixed point: 128-bit products in
 // shared 128-bit accumulators, flushed into 192-bit global accumulators.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "gs_internal.cuh"
@@ -42,11 +44,9 @@ struct Cat {
   const int32_t* __restrict__ deg;
   const uint32_t* __restrict__ adj;  // row j at row_at(adj, ptr, j, adj_off, split, adj_off2)
   int64_t adj_off, split, adj_off2;
-  const int64_t* __restrict__ W;   // exact mode: fixed-point weights
-  const double* __restrict__ Wd;   // FP64 mode: weights
+  const int64_t* __restrict__ W;   // fixed-point weights (weighted launches)
   unsigned long long* counts;  // [nconf]
-  unsigned long long* wacc;    // exact mode: [nconf][3] 192-bit
-  double* wsd;                 // FP64 mode: [nconf] weighted sums
+  unsigned long long* wacc;    // [nconf][3] 192-bit weighted sums
   int64_t hub_begin, hub_end;
 };
 
@@ -61,6 +61,7 @@ struct Args {
   int force_hash;         // 1: every hub takes the hash path
   int stage_cap;          // hub rows up to this many words are staged
   int stage_alloc;        // words of the staging buffer
+  int use_lut;            // 1: configuration index from the shared table
   unsigned long long* hub_counter;
   int* err;
 };
@@ -71,28 +72,25 @@ struct Smem {
   int64_t* wst;        // weighted: stage_alloc staged weights of N+(i) (8 bytes each)
   uint16_t* lut;       // nb^3 configuration indices (or nullptr)
   unsigned* hist;      // nconf
-  unsigned long long* whist;  // FP64: nconf doubles; exact: 2 nconf (lo, hi) words
+  unsigned long long* whist;  // 2 nconf (lo, hi) words
 };
 
 __device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int nb) {
   return sm.lut ? (int)sm.lut[(bij * nb + bik) * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
 }
 
-// Weight modes: kNone, kFp64 (w_i w_j w_k in FP64, per-CTA shared FP64
-// sums, one reduction per triangle) and kExact (fixed-point integers: exact
-// 128-bit products in shared 128-bit accumulators, 192-bit global sums).
-enum : int { kNone = 0, kFp64 = 1, kExact = 2 };
+// Weight modes: kNone and kExact (fixed-point integers: exact 128-bit
+// products in shared 128-bit accumulators, 192-bit global sums; shared FP64
+// reductions measured slower than this on GB300).
+enum : int { kNone = 0, kExact = 2 };
 template <int WM>
-using WType = typename std::conditional<WM == kFp64, double, int64_t>::type;
+using WType = int64_t;
 
 template <int WM, bool SMEM_HIST>
 __device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Wij, WType<WM> Wk) {
   if (SMEM_HIST) atomicAdd(sm.hist + cf, 1u);
   else atomicAdd(c.counts + cf, 1ull);
-  if constexpr (WM == kFp64) {
-    if (SMEM_HIST) atomicAdd(reinterpret_cast<double*>(sm.whist) + cf, Wij * Wk);
-    else atomicAdd(c.wsd + cf, Wij * Wk);
-  } else if constexpr (WM == kExact) {
+  if constexpr (WM == kExact) {
     long long lo, hi;
     mul_i128(Wij, Wk, &lo, &hi);
     if (SMEM_HIST) atomic_add_i128(sm.whist + 2 * cf, lo, hi);
@@ -102,8 +100,7 @@ __device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Wi
 
 template <int WM>
 __device__ inline WType<WM> wget(const Cat& c, int64_t k) {
-  if constexpr (WM == kFp64) return c.Wd[k];
-  else if constexpr (WM == kExact) return c.W[k];
+  if constexpr (WM == kExact) return c.W[k];
   else return 0;
 }
 
@@ -122,8 +119,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     sm.wst = reinterpret_cast<int64_t*>(p);
     if (WEIGHTED) p += (size_t)a.stage_alloc * 8;
     const int nb3 = a.nb * a.nb * a.nb;
-    sm.lut = nb3 <= kLutMax ? reinterpret_cast<uint16_t*>(p) : nullptr;
-    if (sm.lut) p += ((nb3 * 2 + 15) / 16) * 16;
+    sm.lut = (a.use_lut && nb3 <= kLutMax) ? reinterpret_cast<uint16_t*>(p) : nullptr;
+    if (a.use_lut && nb3 <= kLutMax) p += ((nb3 * 2 + 15) / 16) * 16;
     sm.hist = reinterpret_cast<unsigned*>(p);
     p += ((a.nconf * 4 + 15) / 16) * 16;
     sm.whist = reinterpret_cast<unsigned long long*>(p);
@@ -166,13 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         atomicAdd(c.counts + k, (unsigned long long)v);
         sm.hist[k] = 0;
       }
-      if (WM == kFp64) {
-        double* wh = reinterpret_cast<double*>(sm.whist);
-        if (wh[k] != 0.0) {
-          atomicAdd(c.wsd + k, wh[k]);
-          wh[k] = 0.0;
-        }
-      } else if (WM == kExact) {
+      if (WM == kExact) {
         const unsigned long long lo = sm.whist[2 * k], hi = sm.whist[2 * k + 1];
         if (lo | hi) {
           atomic_add_i192(c.wacc + 3 * k, lo, hi);
@@ -345,26 +336,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
             }
           }
           const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+          // all four probes are issued before any hit is handled, so their
+          // shared-memory latencies overlap; keys past the hub row probe
+          // slot 0 and are discarded
+          bool ok[4];
+          uint32_t off[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const uint32_t key = edge_id(vv[q]);
-            if (key > hub_hi) continue;
-            const uint32_t off = key - base;
-            if (WEIGHTED) {
-              const uint32_t bw = bm[off >> 5];
-              const uint32_t bit = 1u << (off & 31);
-              if (bw & bit) {
-                const int pos = (int)pre[off >> 5] + __popc(bw & (bit - 1u));
+            ok[q] = key <= hub_hi;
+            off[q] = ok[q] ? key - base : 0u;
+          }
+          if (WEIGHTED) {
+            uint32_t bw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bw[q] = bm[off[q] >> 5];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t bit = 1u << (off[q] & 31);
+              if (ok[q] && (bw[q] & bit)) {
+                const int pos = (int)pre[off[q] >> 5] + __popc(bw[q] & (bit - 1u));
                 record<WM, SMEM_HIST>(
                     sm, c, conf_index(sm, bij, (int)edge_bin(hr[pos]), (int)edge_bin(vv[q]), nb),
                     Wij, wst[pos]);
               }
-            } else {
-              const uint8_t bik = sm.table[off];
-              if (bik != kAbsent)
-                record<WM, SMEM_HIST>(sm, c, conf_index(sm, bij, bik, (int)edge_bin(vv[q]), nb),
-                                      WT(0), WT(0));
             }
+          } else {
+            uint8_t bik[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bik[q] = sm.table[off[q]];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (ok[q] && bik[q] != kAbsent)
+                record<WM, SMEM_HIST>(sm, c, conf_index(sm, bij, bik[q], (int)edge_bin(vv[q]), nb),
+                                      WT(0), WT(0));
           }
           if (more) {
             t0 += 128;
@@ -482,7 +487,7 @@ struct Count3Launch {
   bool smem_hist = true;
 };
 
-Count3Launch count3_launch(int nb, int nconf, int wmode) {
+Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut) {
   const bool weighted = wmode != kNone;
   // weighted launches stage rows and weights of up to 2048 neighbours
   int dev = 0, optin = 0;
@@ -490,8 +495,8 @@ Count3Launch count3_launch(int nb, int nconf, int wmode) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   const size_t nb3 = (size_t)nb * nb * nb;
-  const size_t lut = nb3 <= (size_t)kLutMax ? pad16(nb3 * 2) : 0;
-  size_t hist = pad16((size_t)nconf * 4) + (size_t)nconf * (wmode == kExact ? 16 : wmode == kFp64 ? 8 : 0);
+  const size_t lut = (use_lut && nb3 <= (size_t)kLutMax) ? pad16(nb3 * 2) : 0;
+  size_t hist = pad16((size_t)nconf * 4) + (size_t)nconf * (wmode == kExact ? 16 : 0);
   Count3Launch L;
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
   const size_t stage_words = weighted ? 2048 : kStageCap;
@@ -554,8 +559,12 @@ __global__ void k_u64_to_double(const unsigned long long* c, int64_t n, double* 
     out[k] = (double)c[k];
 }
 
+int resolve_variant(const Graph& g, int wmode, int variant);
+
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
-                  const Opts& o, Scratch& sc) {
+                  const Opts& o_in, Scratch& sc) {
+  Opts o = o_in;
+  o.variant = resolve_variant(g, (fw && d_wsum) ? 2 : 0, o.variant);
   cudaStream_t s = o.stream;
   const int nconf = (int)num_conf3(g.nb);
   Args a;
@@ -577,31 +586,28 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.one.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.one.W = fw ? fw->d_W : nullptr;
-  a.one.Wd = fw ? fw->d_Wd : nullptr;
-  const int wm = (fw && d_wsum) ? (o.exact_weights ? kExact : kFp64) : kNone;
+  const int wm = (fw && d_wsum) ? kExact : kNone;
   a.one.wacc = wm == kExact ? sc.alloc<unsigned long long>(3 * (size_t)nconf) : nullptr;
-  a.one.wsd = wm == kFp64 ? d_wsum : nullptr;
   a.hub_counter = sc.alloc<unsigned long long>(1);
   a.err = sc.alloc<int>(1);
   if (!a.hub_counter || !a.err || (wm == kExact && !a.one.wacc)) return GS_ENOMEM;
   cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * nconf, s);
   if (wm == kExact) cudaMemsetAsync(a.one.wacc, 0, sizeof(unsigned long long) * 3 * nconf, s);
-  if (wm == kFp64) cudaMemsetAsync(d_wsum, 0, sizeof(double) * nconf, s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   if (g.n == 0) {
     if (d_wsum) cudaMemsetAsync(d_wsum, 0, sizeof(double) * nconf, s);
     return cuda_status(cudaGetLastError());
   }
 
-  const Count3Launch L = count3_launch(g.nb, nconf, wm);
+  const Count3Launch L = count3_launch(g.nb, nconf, wm, (o.variant & 4) != 0);
   a.span_cap = L.span_cap;
   a.stage_alloc = L.stage_words;
+  a.use_lut = (o.variant & 4) ? 1 : 0;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
   if (wm == kExact) kern = smem_hist ? k_count3<kExact, true, false> : k_count3<kExact, false, false>;
-  else if (wm == kFp64) kern = smem_hist ? k_count3<kFp64, true, false> : k_count3<kFp64, false, false>;
   else kern = smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
@@ -640,11 +646,13 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
 }
 
 int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
-                        double* const* d_wsum, const Opts& o, Scratch& sc) {
+                        double* const* d_wsum, const Opts& o_in, Scratch& sc) {
+  Opts o = o_in;
+  o.variant = resolve_variant(*gr[0], (fws && d_wsum) ? 2 : 0, o.variant);
   cudaStream_t s = o.stream;
   const int nb = gr[0]->nb;
   const int nconf = (int)num_conf3(nb);
-  const int wm = (fws && d_wsum) ? (o.exact_weights ? kExact : kFp64) : kNone;
+  const int wm = (fws && d_wsum) ? kExact : kNone;
   std::vector<Cat> cats(ng);
   std::vector<int64_t> base(ng + 1, 0);
   unsigned long long* wacc =
@@ -660,15 +668,8 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
     c.split = g.n;
     c.adj_off2 = 0;
     c.W = fws ? fws[k].d_W : nullptr;
-    c.Wd = fws ? fws[k].d_Wd : nullptr;
     c.counts = reinterpret_cast<unsigned long long*>(d_counts[k]);
     c.wacc = wm == kExact ? wacc + 3 * (size_t)nconf * k : nullptr;
-    c.wsd = nullptr;
-    if (wm == kFp64) {  // a catalogue without a wsum output still needs somewhere to add
-      c.wsd = d_wsum[k] ? d_wsum[k] : sc.alloc<double>(nconf);
-      if (!c.wsd) return GS_ENOMEM;
-      cudaMemsetAsync(c.wsd, 0, sizeof(double) * nconf, s);
-    }
     c.hub_begin = 0;
     c.hub_end = g.n;
     base[k + 1] = base[k] + g.n;
@@ -694,15 +695,15 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
-  const Count3Launch L = count3_launch(nb, nconf, wm);
+  const Count3Launch L = count3_launch(nb, nconf, wm, (o.variant & 4) != 0);
   a.span_cap = L.span_cap;
   a.stage_alloc = L.stage_words;
+  a.use_lut = (o.variant & 4) ? 1 : 0;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
   if (wm == kExact) kern = smem_hist ? k_count3<kExact, true, true> : k_count3<kExact, false, true>;
-  else if (wm == kFp64) kern = smem_hist ? k_count3<kFp64, true, true> : k_count3<kFp64, false, true>;
   else kern = smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
@@ -823,10 +824,8 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.one.split = g.n;
     a.one.adj_off2 = 0;
     a.one.W = nullptr;
-    a.one.Wd = nullptr;
     a.one.counts = reinterpret_cast<unsigned long long*>(dc);
     a.one.wacc = nullptr;
-    a.one.wsd = nullptr;
     a.one.hub_begin = 0;
     a.one.hub_end = g.n;
     a.cats = nullptr;
@@ -839,9 +838,10 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
     a.hub_counter = counter;
     a.err = err;
-    const Count3Launch L = count3_launch(g.nb, nconf, kNone);
+    const Count3Launch L = count3_launch(g.nb, nconf, kNone, (o.variant & 4) != 0);
     a.span_cap = L.span_cap;
     a.stage_alloc = L.stage_words;
+    a.use_lut = (o.variant & 4) ? 1 : 0;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
     void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
@@ -906,10 +906,8 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
     c.split = g.n;
     c.adj_off2 = 0;
     c.W = nullptr;
-    c.Wd = nullptr;
     c.counts = reinterpret_cast<unsigned long long*>(counts[k]);
     c.wacc = nullptr;
-    c.wsd = nullptr;
     c.hub_begin = 0;
     c.hub_end = g.n;
     base[k + 1] = base[k] + g.n;
@@ -935,9 +933,10 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.hub_counter = P->counter;
   a.err = P->err;
-  const Count3Launch L = count3_launch(nb, nconf, kNone);
+  const Count3Launch L = count3_launch(nb, nconf, kNone, (o.variant & 4) != 0);
   a.span_cap = L.span_cap;
   a.stage_alloc = L.stage_words;
+  a.use_lut = (o.variant & 4) ? 1 : 0;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
   int per_sm = 0, sms = 0, dev = 0;
@@ -991,4 +990,81 @@ extern "C" void gs_plan_destroy(gs_plan* P) {
   cudaFree(P->d_base);
   cudaFree(P->counter);
   delete P;
+}
+
+// ----------------------------------------------------------------------------
+// Autotuning of the 3pCF launch choices. gs_tune_3pcf times the candidate
+// variants on one hub shard of the caller's graph (a contiguous sample of
+// about 1/16 of its edges) and remembers the fastest for graphs with the
+// same bin count, weight mode and degree class; queries with variant -1
+// use it (variant 0 when nothing has been tuned).
+namespace gs {
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+std::tuple<int, int, int> tune_key(const Graph& g, int wmode) {
+  const double mean = g.n ? (double)g.edges_total / (double)g.n : 0.0;
+  int cls = 0;
+  while (cls < 30 && (double)(1 << cls) < mean) ++cls;
+  return {g.nb, wmode, cls};
+}
+}  // namespace
+
+int resolve_variant(const Graph& g, int wmode, int variant) {
+  if (variant >= 0) return variant;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(tune_key(g, wmode));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+}  // namespace gs
+
+extern "C" int gs_tune_3pcf(const gs_graph* G, const float* w, const gs_options* options,
+                            int32_t* best_variant) {
+  using namespace gs;
+  if (!G || !best_variant) return GS_EINVAL;
+  const Graph& g = G->g;
+  Opts o = read_opts(options);
+  const int nconf = (int)num_conf3(g.nb);
+  const int wmode = w ? kExact : kNone;
+  static const int kCandidates[4] = {0, 2, 4, 6};
+  int best = 0;
+  double best_ms = 1e300;
+  int st = GS_OK;
+  {
+    Scratch sc(o.stream);
+    FixedW fw;
+    if (w) {
+      st = prepare_weights(g, w, &fw, sc, o.stream);
+      if (st) return st;
+    }
+    uint64_t* dc = sc.alloc<uint64_t>(nconf);
+    double* dw = w ? sc.alloc<double>(nconf) : nullptr;
+    if (!dc || (w && !dw)) return GS_ENOMEM;
+    for (int c : kCandidates) {
+      double ms = 0.0;
+      for (int rep = 0; rep < 2 && !st; ++rep) {  // the first run warms caches up
+        Opts t = o;
+        t.variant = c;
+        t.shard = 0;
+        t.shards = 16;
+        double k = 0.0;
+        t.kernel_ms = &k;
+        Scratch run(o.stream);
+        st = count3_device(g, w ? &fw : nullptr, dc, dw, t, run);
+        ms = k;
+      }
+      if (st) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[tune_key(g, wmode)] = best;
+  }
+  *best_variant = best;
+  return GS_OK;
 }

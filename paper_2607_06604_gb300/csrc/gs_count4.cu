@@ -29,7 +29,7 @@
 namespace gs {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSmemRow = 512;
 
@@ -140,7 +140,7 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
 // when the staging copy timed out.
 template <bool PARITY, bool WEIGHTED, bool SMALLR, bool GW, class E2T>
 __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned* h_even,
-                     int* h_odd, int64_t i, int m, uint64_t* bar, uint32_t& phase) {
+                     int* h_odd, int64_t i, int m, uint64_t* bar, uint32_t& phase, int* s_row) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = a.nb;
   const int W = (m + 31) / 32;
@@ -177,6 +177,7 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned*
     while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
   }
   __syncthreads();
+  if (tid == 0) *s_row = 0;
   // bit matrix: row a gets bit c for every c > a adjacent to j_a
   const uint32_t hub_hi = edge_id(row[m - 1]);
   for (int sa = warp; sa < m - 1; sa += kWarps) {
@@ -216,7 +217,13 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned*
   const int64_t Wi = WEIGHTED ? a.W[i] : 0;
   uint32_t* qbc = w.queue + warp * 64;
   uint8_t* qb12 = reinterpret_cast<uint8_t*>(w.queue + kWarps * 64) + warp * 64;
-  for (int sa = warp; sa < m - 2; sa += kWarps) {
+  // rows near the start of N+(i) carry most of the work: warps take rows
+  // from a shared counter (reset by thread 0 before the bit matrix was built)
+  for (;;) {
+    int sa = 0;
+    if (lane == 0) sa = atomicAdd(s_row, 1);
+    sa = __shfl_sync(0xffffffffu, sa, 0);
+    if (sa >= m - 2) break;
     const uint32_t wa = row[sa];
     const int b01 = (int)edge_bin(wa);
     const int4 da = w.disp[sa];
@@ -324,6 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   __shared__ int s_flush;
   __shared__ unsigned long long s_pending;
   __shared__ E2T e2[kMaxBins4 + 1];
+  __shared__ int s_row;
 
   const int tid = threadIdx.x;
   unsigned* h_even = reinterpret_cast<unsigned*>(smem);
@@ -405,9 +413,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     const int m = a.deg[i];
     bool ok;
     if (m > a.thr)
-      ok = hub4<PARITY, WEIGHTED, SMALLR, true>(a, ws_g, e2, h_even, h_odd, i, m, &bar, phase);
+      ok = hub4<PARITY, WEIGHTED, SMALLR, true>(a, ws_g, e2, h_even, h_odd, i, m, &bar, phase,
+                                                &s_row);
     else
-      ok = hub4<PARITY, WEIGHTED, SMALLR, false>(a, ws_s, e2, h_even, h_odd, i, m, &bar, phase);
+      ok = hub4<PARITY, WEIGHTED, SMALLR, false>(a, ws_s, e2, h_even, h_odd, i, m, &bar, phase,
+                                                 &s_row);
     if (!ok) return;
   }
   __syncthreads();

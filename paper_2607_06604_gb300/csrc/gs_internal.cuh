@@ -91,7 +91,6 @@ struct Opts {
   cudaStream_t stream = nullptr;
   double* kernel_ms = nullptr;
   int shard = 0, shards = 0;
-  bool exact_weights = false;
 };
 
 // Hub range [lo, hi) of the query's shard (the whole graph when unsharded).
@@ -151,7 +150,6 @@ int64_t num_conf3(int nb);
 // Fixed-point weights: W_i = w_i * 2^scale is an integer for every point.
 struct FixedW {
   int64_t* d_W = nullptr;  // [n], internal order
-  double* d_Wd = nullptr;  // [n], the same weights as doubles
   int scale = 0;
   int bits = 0;  // max bit length of |W_i| plus one sign bit
 };

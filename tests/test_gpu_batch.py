@@ -43,10 +43,10 @@ def test_batch_equals_single_and_oracle(gs):
             assert np.array_equal(c.cpu().numpy(), rc)
             np.testing.assert_allclose(s.cpu().numpy(), rw, rtol=1e-12)
     # exact weighted sums are identical in and out of a batch
-    out_x = gs.gs_count_3pcf_batch(graphs, ws, exact=True)
+    out_x = gs.gs_count_3pcf_batch(graphs, ws)
     for k in range(len(sizes)):
         assert np.array_equal(out_x[k][1].cpu().numpy(),
-                              gs.gs_count_3pcf(graphs[k], ws[k], exact=True)[1].cpu().numpy())
+                              gs.gs_count_3pcf(graphs[k], ws[k])[1].cpu().numpy())
     # unweighted batch, host outputs
     out_u = gs.gs_count_3pcf_batch(graphs)
     for k in range(len(sizes)):
@@ -81,3 +81,19 @@ def test_recorded_plan_replays_exactly(gs):
         for c, r in zip(counts, refs):
             assert np.array_equal(c.cpu().numpy(), r)
     plan.close()
+
+
+def test_autotuner_picks_a_variant_with_identical_counts(gs):
+    L = 100.0
+    box_u = int(L * 1024)
+    edges = catalogs.bin_edges_u(0.0, 9.0, 6)
+    X = oracle.quantize(catalogs.neyman_scott(20_000, L, seed=700, sigma=1.5), box_u, True)
+    w = catalogs.uniform_weights(X.shape[0], seed=701)
+    g = gs.gs_build_graph(X, box_u, edges)
+    ref_c, ref_w = gs.gs_count_3pcf(g, w)
+    best = gs.gs_tune_3pcf(g, w)
+    assert best in (0, 2, 4, 6)
+    c, ws = gs.gs_count_3pcf(g, w, variant=-1)
+    assert np.array_equal(c, ref_c) and np.array_equal(ws, ref_w)
+    assert gs.gs_tune_3pcf(g) in (0, 2, 4, 6)
+    assert np.array_equal(gs.gs_count_3pcf(g, variant=-1), ref_c)

@@ -36,7 +36,7 @@ def resident(gs, case):
     X, box_u, edges, w = case
     g = gs.gs_build_graph(X, box_u, edges)
     assert gs.gs_graph_info(g)["windows"] == 1
-    out = {"c3": gs.gs_count_3pcf(g, w, exact=True), "c3f": gs.gs_count_3pcf(g, w),
+    out = {"c3": gs.gs_count_3pcf(g, w), "c3f": gs.gs_count_3pcf(g, w),
            "c4": gs.gs_count_4pcf_parity(g),
            "pairs": gs.gs_disconnected_4pcf(g, w), "export": gs.gs_graph_export(g),
            "info": gs.gs_graph_info(g)}
@@ -54,7 +54,7 @@ def test_forced_windows_bit_identical(gs, case, resident, windows):
     g = gs.gs_build_graph(X, box_u, edges, force_windows=windows)
     info = gs.gs_graph_info(g)
     assert info["windows"] == windows or (windows > 1 and info["windows"] > 1)
-    c, ws = gs.gs_count_3pcf(g, w, exact=True)
+    c, ws = gs.gs_count_3pcf(g, w)
     assert np.array_equal(c, resident["c3"][0])
     assert np.array_equal(ws, resident["c3"][1])  # exact sums: bit-identical
     _, wf = gs.gs_count_3pcf(g, w)
@@ -80,7 +80,7 @@ def test_budget_driven_windows(gs, case, resident):
     g = gs.gs_build_graph(X, box_u, edges, budget=budget)
     info = gs.gs_graph_info(g)
     assert info["windows"] >= 2
-    c, ws = gs.gs_count_3pcf(g, w, exact=True)
+    c, ws = gs.gs_count_3pcf(g, w)
     assert np.array_equal(c, resident["c3"][0]) and np.array_equal(ws, resident["c3"][1])
     # a query may ask for smaller windows than the build did
     c2 = gs.gs_count_3pcf(g, budget=int(budget * 0.75))

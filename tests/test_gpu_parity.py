@@ -1,9 +1,9 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
 Unweighted counts, pair counts and lattice coordinates must match bit for
-bit; weighted sums, xi and zeta_disc within 1e-12 relative (both sides sum
-exactly and round once, so the only differences come from the final
-rounding and from FP64 evaluation order of RR).
+bit; weighted sums, xi and zeta_disc within 1e-12 relative (the oracle sums
+exactly; the GPU sums in FP64, or exactly with GS_FLAG_EXACT_WEIGHTS, and
+xi / zeta_disc differ only by FP64 evaluation order of RR).
 """
 import json
 import math
@@ -173,15 +173,15 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     # every kernel path gives the same answer: hash path in 64-word segments
     # (variant 1) and the table path reading hub rows from global (variant 2)
     g = gs.gs_build_graph(X, bu, edges)
-    ex_c, ex_w = gs.gs_count_3pcf(g, w, exact=True)
+    ex_c, ex_w = gs.gs_count_3pcf(g, w)
     assert np.array_equal(ex_c, rc)
     np.testing.assert_allclose(ex_w, rw, rtol=RTOL)
-    for variant in (1, 2):
+    for variant in (1, 2, 4, 6):
         vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(vc, rc), variant
         np.testing.assert_allclose(vw, gw, rtol=1e-13)
         # exact sums are identical bit for bit whichever path found them
-        assert np.array_equal(gs.gs_count_3pcf(g, w, variant=variant, exact=True)[1], ex_w)
+        assert np.array_equal(gs.gs_count_3pcf(g, w, variant=variant)[1], ex_w)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
@@ -221,7 +221,7 @@ def test_3pcf_long_rows_segmented(gs, torch_mod, periodic):
     gc, gw = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1)
     assert np.array_equal(gc.cpu().numpy(), rc)
     np.testing.assert_allclose(gw.cpu().numpy(), rw, rtol=RTOL)
-    _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1, exact=True)
+    _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1)
     np.testing.assert_allclose(gx.cpu().numpy(), rw, rtol=RTOL)
 
 
@@ -368,7 +368,7 @@ def test_full_size_ddd_bit_exact(gs, torch_mod, ns1m):
     assert np.array_equal(gc, rc)
     np.testing.assert_allclose(gw, rw, rtol=RTOL)
     g = gs.gs_build_graph(dev(torch_mod, X), s["box_u"], s["edges_u"])
-    _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w), exact=True)
+    _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w))
     np.testing.assert_allclose(gx.cpu().numpy(), rw, rtol=RTOL)
 
 
