@@ -75,8 +75,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_VERSION = "k_count3.v8"  # bump when k_count3 changes; stale captures then report null
+
+
 def recorded_traffic():
-    """Per-launch DRAM bytes of the counting kernel from the committed ncu summary."""
+    """Per-launch DRAM bytes of the counting kernel from the committed ncu
+    summary, or None when that capture predates the current kernel."""
     p = os.path.join(ROOT, "profiles", "count3_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -85,6 +89,8 @@ def recorded_traffic():
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             vals[k.strip()] = v.strip()
+    if vals.get("kernel_version") != KERNEL_VERSION:
+        return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])
     except (KeyError, ValueError):
@@ -332,6 +338,8 @@ def run_ours(args):
     traffic = recorded_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "limiter": "shared-memory pipe (random table probes and 64-bit atomics; "
+                       "ncu: L1/shared 84% busy, L2 hit 98.9%, DRAM 0.05%)",
             "kernel": "k_count3 (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
             "triangles_per_launch": float(counts[1].sum().item())}
 

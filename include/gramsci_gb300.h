@@ -70,8 +70,10 @@ typedef struct {
    * in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
    * global memory). 2 = gs_count_3pcf reads hub rows from global memory
    * instead of staging them. 4 = gs_count_3pcf looks configuration indices
-   * up in a shared table instead of computing them. Results are identical;
-   * the bits exist for testing and tuning. */
+   * up in a shared table instead of computing them. 8 = gs_count_3pcf
+   * limits its direct-address table to 2 KB (rows split at their largest id
+   * gap, or hashed). Results are identical; the bits exist for testing and
+   * tuning. */
   int32_t variant;
   /* cudaStream_t for all device work; NULL = legacy default stream. */
   void* stream;

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   __shared__ unsigned long long s_pending;
   __shared__ int s_flush, s_cat, s_cur, s_next;
   __shared__ int s_warp_sum[kWarps];
+  __shared__ unsigned long long s_red[kWarps];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = a.nb;
@@ -247,22 +248,70 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     // weighted hubs need their row and weights staged (positions come from
     // the bitmap rank); the bitmap + 16-bit prefix take 6 bytes per 32 ids
     const int64_t table_span = WEIGHTED ? (int64_t)(a.span_cap / 6) * 32 : (int64_t)a.span_cap;
-    if (!a.force_hash && span <= table_span && (!WEIGHTED || staged)) {
-      // ---------------- direct-address table path
+    bool use_table = !a.force_hash && (!WEIGHTED || staged);
+    // The table covers ids [i+1, near_hi] at offsets 0 .. len1-1 and, for
+    // rows split at their largest id gap (wrap-around neighbours of a
+    // periodic box), [far_lo, hub_hi] after them.
+    uint32_t near_hi = hub_hi, far_lo = hub_hi + 1u;
+    int64_t len1 = span, tspan = span;
+    const uint32_t* hr = row;
+    if (use_table) {
       if (staged) {
         if (tid == 0) bulk_load(sm.stage, row, (uint32_t)pad_row(d) * 4u, &bar);
+        // weighted: staged word = 256 W_k + bin(i, k), one load per hit
         if (WEIGHTED)
-          for (int k = tid; k < d; k += kThreads) wst[k] = wget<WM>(c, edge_id(row[k]));
+          for (int k = tid; k < d; k += kThreads) {
+            const uint32_t w = row[k];
+            wst[k] = wget<WM>(c, edge_id(w)) * 256 + (WT)edge_bin(w);
+          }
         if (!wait_stage()) return;
+        hr = sm.stage;
       }
-      const uint32_t* hr = staged ? sm.stage : row;
+      if (span > table_span) {
+        // largest gap between consecutive neighbour ids (first one on ties)
+        unsigned long long best = 0ull;
+        for (int k = tid; k < d - 1; k += kThreads) {
+          const unsigned long long gap = edge_id(hr[k + 1]) - edge_id(hr[k]);
+          const unsigned long long key = (gap << 32) | (0xFFFFFFFFull - (unsigned long long)k);
+          best = best > key ? best : key;
+        }
+        for (int o = 16; o; o >>= 1) {
+          const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+          best = best > y ? best : y;
+        }
+        if (lane == 0) s_red[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+          best = s_red[lane];
+          for (int o = 16; o; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+            best = best > y ? best : y;
+          }
+          if (lane == 0) s_red[0] = best;
+        }
+        __syncthreads();
+        const int ks = (int)(0xFFFFFFFFull - (s_red[0] & 0xFFFFFFFFull));
+        __syncthreads();
+        near_hi = edge_id(hr[ks]);
+        far_lo = edge_id(hr[ks + 1]);
+        len1 = (int64_t)near_hi - i;
+        tspan = len1 + ((int64_t)hub_hi - far_lo + 1);
+        use_table = tspan <= table_span;
+      }
+    }
+    if (use_table) {
+      // ---------------- direct-address table path
       const uint32_t base = (uint32_t)(i + 1);
+      const uint32_t far_off = (uint32_t)len1;
+      auto slot = [&](uint32_t key) -> uint32_t {
+        return key <= near_hi ? key - base : key - far_lo + far_off;
+      };
       uint32_t* bm = reinterpret_cast<uint32_t*>(sm.table);
-      const int nw = (int)((span + 31) >> 5);
+      const int nw = (int)((tspan + 31) >> 5);
       uint16_t* pre = reinterpret_cast<uint16_t*>(bm + nw);
       if (WEIGHTED) {
         for (int k = tid; k < d; k += kThreads) {
-          const uint32_t off = edge_id(hr[k]) - base;
+          const uint32_t off = slot(edge_id(hr[k]));
           atomicOr(bm + (off >> 5), 1u << (off & 31));
         }
         __syncthreads();
@@ -295,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       } else {
         for (int k = tid; k < d; k += kThreads) {
           const uint32_t w = hr[k];
-          sm.table[edge_id(w) - base] = (uint8_t)edge_bin(w);
+          sm.table[slot(edge_id(w))] = (uint8_t)edge_bin(w);
         }
       }
       __syncthreads();
@@ -314,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
         for (;;) {
           const int bij = (int)edge_bin(wij);
-          const WT Wij = Wi * (staged ? wst[sp] : wget<WM>(c, edge_id(wij)));
+          const WT Wij = Wi * (staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij)));
           const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
           const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
           uint4 vn = none;
@@ -344,8 +393,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const uint32_t key = edge_id(vv[q]);
-            ok[q] = key <= hub_hi;
-            off[q] = ok[q] ? key - base : 0u;
+            ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo);
+            off[q] = ok[q] ? slot(key) : 0u;
           }
           if (WEIGHTED) {
             uint32_t bw[4];
@@ -356,9 +405,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               const uint32_t bit = 1u << (off[q] & 31);
               if (ok[q] && (bw[q] & bit)) {
                 const int pos = (int)pre[off[q] >> 5] + __popc(bw[q] & (bit - 1u));
+                const WT packed = wst[pos];
                 record<WM, SMEM_HIST>(
-                    sm, c, conf_index(sm, bij, (int)edge_bin(hr[pos]), (int)edge_bin(vv[q]), nb),
-                    Wij, wst[pos]);
+                    sm, c, conf_index(sm, bij, (int)(packed & 0xFF), (int)edge_bin(vv[q]), nb),
+                    Wij, packed >> 8);
               }
             }
           } else {
@@ -387,10 +437,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       __syncthreads();
       if (WEIGHTED) {
         // the next hub's bitmap may extend over this hub's prefix words
-        for (int k = tid; k < d; k += kThreads) bm[(edge_id(hr[k]) - base) >> 5] = 0u;
+        for (int k = tid; k < d; k += kThreads) bm[slot(edge_id(hr[k])) >> 5] = 0u;
         for (int q = tid; q < (nw + 1) / 2; q += kThreads) bm[nw + q] = 0u;
       } else {
-        for (int k = tid; k < d; k += kThreads) sm.table[edge_id(hr[k]) - base] = kAbsent;
+        for (int k = tid; k < d; k += kThreads) sm.table[slot(edge_id(hr[k]))] = kAbsent;
       }
       __syncthreads();
       continue;
@@ -600,7 +650,7 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   }
 
   const Count3Launch L = count3_launch(g.nb, nconf, wm, (o.variant & 4) != 0);
-  a.span_cap = L.span_cap;
+  a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
@@ -696,7 +746,7 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   const Count3Launch L = count3_launch(nb, nconf, wm, (o.variant & 4) != 0);
-  a.span_cap = L.span_cap;
+  a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
@@ -839,7 +889,7 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.hub_counter = counter;
     a.err = err;
     const Count3Launch L = count3_launch(g.nb, nconf, kNone, (o.variant & 4) != 0);
-    a.span_cap = L.span_cap;
+    a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
     a.stage_alloc = L.stage_words;
     a.use_lut = (o.variant & 4) ? 1 : 0;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
@@ -934,7 +984,7 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.hub_counter = P->counter;
   a.err = P->err;
   const Count3Launch L = count3_launch(nb, nconf, kNone, (o.variant & 4) != 0);
-  a.span_cap = L.span_cap;
+  a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);

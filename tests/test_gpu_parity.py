@@ -176,7 +176,7 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     ex_c, ex_w = gs.gs_count_3pcf(g, w)
     assert np.array_equal(ex_c, rc)
     np.testing.assert_allclose(ex_w, rw, rtol=RTOL)
-    for variant in (1, 2, 4, 6):
+    for variant in (1, 2, 4, 6, 8, 10):
         vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(vc, rc), variant
         np.testing.assert_allclose(vw, gw, rtol=1e-13)
@@ -391,3 +391,42 @@ def test_full_size_rrr_properties(gs, torch_mod):
     expect = math.comb(N, 3) * p * p * 15 / 32
     sd = math.sqrt(expect) * 30  # generous: triangle counts are strongly correlated
     assert abs(float(c0.sum()) - expect) < 5 * sd
+
+
+def test_4pcf_parity_clustered_workload_density(gs, torch_mod):
+    """Neyman-Scott points at the density of the 2e5-point L=400 workload
+    (2.5e4 points, L=200; mean degree about 360), rmax 30 in 8 bins: every
+    even and odd bin against the oracle (the full 2e5 catalogue takes the
+    oracle many minutes)."""
+    L = 200.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(25_000, L, seed=4, sigma=2.0)
+    X = oracle.quantize(pos, box_u, True)
+    edges = catalogs.bin_edges_u(0.0, 30.0, 8)
+    og = oracle.Graph(X, box_u, edges)
+    re, ro = og.count_4pcf()
+    ge, go = run4(gs, torch_mod, X, box_u, edges)
+    assert re.sum() > 1e9
+    assert np.array_equal(ge, re) and np.array_equal(go, ro)
+
+
+def test_full_size_out_of_core_workload(gs, torch_mod):
+    """1e6 Neyman-Scott points (sigma 5) in an open box L=1494, rmax 150 in 15
+    bins (about 1.2e12 triangles, too many for the oracle): a graph streamed
+    in forced windows counts exactly what the resident graph counts, and the
+    mirror image x -> L-1-x counts the same."""
+    s = catalogs.draw("ns1M_open_L1494_r150_nb15")
+    box_u, edges = s["box_u"], s["edges_u"]
+    X = oracle.quantize(s["pos"], box_u, False)
+    Xd = dev(torch_mod, X)
+    c0 = gs.gs_count_3pcf(gs.gs_build_graph(Xd, 0, edges), like=Xd).cpu().numpy()
+    assert c0.sum() > 1e12
+    g3 = gs.gs_build_graph(Xd, 0, edges, force_windows=3)
+    assert gs.gs_graph_info(g3)["windows"] >= 3
+    assert np.array_equal(gs.gs_count_3pcf(g3, like=Xd).cpu().numpy(), c0)
+    del g3
+    Xm = X.copy()
+    Xm[:, 0] = (box_u - 1 - Xm[:, 0].astype(np.int64)).astype(np.int32)
+    Xmd = dev(torch_mod, Xm)
+    cm = gs.gs_count_3pcf(gs.gs_build_graph(Xmd, 0, edges), like=Xmd).cpu().numpy()
+    assert np.array_equal(cm, c0)
