@@ -62,6 +62,7 @@ struct Args {
   int stage_cap;          // hub rows up to this many words are staged
   int stage_alloc;        // words of the staging buffer
   int use_lut;            // 1: configuration index from the shared table
+  uint32_t first_wait_limit;  // polls allowed for a block's first staging wait
   unsigned long long* hub_counter;
   int* err;
 };
@@ -174,13 +175,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     }
   };
   // bounded wait on the bulk copy; false when it timed out (block-uniform)
+  // On an expired wait the block reports it, then waits (bounded again) for
+  // its own copy to land before giving up, so no copy outlives the block.
+  // a.first_wait_limit replaces the first wait's budget (tests use 0).
+  uint32_t wait_budget = a.first_wait_limit;
   auto wait_stage = [&]() -> bool {
-    const bool ok = mbar_wait(&bar, phase, kWaitLimit);
-    phase ^= 1u;
+    const bool ok = mbar_wait(&bar, phase, wait_budget);
+    wait_budget = kWaitLimit;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicOr(a.err, kErrTimeout);
+      if (!ok) mbar_wait(&bar, phase, kWaitLimit);
+      __syncthreads();
       return false;
     }
+    phase ^= 1u;
     return true;
   };
 
@@ -653,6 +661,7 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
+  a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
@@ -749,6 +758,7 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
+  a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
@@ -892,6 +902,7 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
     a.stage_alloc = L.stage_words;
     a.use_lut = (o.variant & 4) ? 1 : 0;
+    a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
     void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
@@ -987,6 +998,7 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
+  a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
   int per_sm = 0, sms = 0, dev = 0;

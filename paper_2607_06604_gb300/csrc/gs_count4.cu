@@ -158,11 +158,14 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned*
   for (int k = tid; k < m * W; k += kThreads) w.bits[k] = 0u;
   if (!GW) {
     const bool ok = mbar_wait(bar, phase, kWaitLimit);
-    phase ^= 1u;
     if (__syncthreads_or(!ok)) {
+      // report, then wait (bounded) for the copy to land before giving up
       if (tid == 0) atomicOr(a.err, kErrTimeout);
+      if (!ok) mbar_wait(bar, phase, kWaitLimit);
+      __syncthreads();
       return false;
     }
+    phase ^= 1u;
   } else {
     __syncthreads();
   }
