@@ -75,6 +75,8 @@ def _load():
     lib.or_pairs.restype = ci
     lib.or_disconnected.argtypes = [P, P, P, P, P, P]
     lib.or_disconnected.restype = ci
+    lib.or_connected_4pcf.argtypes = [P, P, P, P, P, P, P, P, P, ci]
+    lib.or_connected_4pcf.restype = ci
     _lib = lib
     return lib
 
@@ -185,3 +187,20 @@ class Graph:
         if st != 0:
             raise ValueError(f"oracle disconnected failed ({st})")
         return p, xi, z
+
+
+def connected_4pcf(g_dr: Graph, w_signed, g_r: Graph, w_r):
+    """Signed-weight connected 4pCF (Sec. 3.3): dict of xi, zeta_even,
+    zeta_odd, zeta_disc, zeta_conn."""
+    nb = g_dr.nb
+    nc = num_configs(4, nb)
+    out = {k: np.zeros(nb if k == "xi" else nc) for k in
+           ("xi", "zeta_even", "zeta_odd", "zeta_disc", "zeta_conn")}
+    ws = np.ascontiguousarray(w_signed, dtype=np.float32)
+    wr = np.ascontiguousarray(w_r, dtype=np.float32)
+    st = _load().or_connected_4pcf(g_dr._h, _ptr(ws), g_r._h, _ptr(wr), _ptr(out["xi"]),
+                                   _ptr(out["zeta_even"]), _ptr(out["zeta_odd"]),
+                                   _ptr(out["zeta_disc"]), _ptr(out["zeta_conn"]), g_dr.nthreads)
+    if st != 0:
+        raise ValueError(f"oracle connected 4pCF failed ({st})")
+    return out

@@ -754,4 +754,57 @@ int or_disconnected(void* gp, const float* w, const double* rr, uint64_t* pairs,
   return 0;
 }
 
+// Sec. 3.3 (Eq. disc, Eq. conn) with the signed-weight estimator of Sec. 2.1:
+// g_dr holds data and randoms together with data weights summing to +1 and
+// random weights to -1; g_r holds the randoms alone with weights summing to
+// +1. Then, per radial bin and per 4-point configuration,
+//   xi        = (signed pair sum) / (random pair sum), no additive constant;
+//   zeta_even = NNNN_even / RRRR, zeta_odd = NNNN_odd / RRRR;
+//   zeta_disc = Eq. (disc) on xi; zeta_conn = zeta_even - zeta_disc
+// (the disconnected part is parity-even and leaves the odd channel alone).
+// Any output may be NULL. Returns 0, -2 when weights cannot be summed exactly.
+int or_connected_4pcf(void* g_dr, const float* w_signed, void* g_r, const float* w_r, double* xi,
+                      double* zeta_even, double* zeta_odd, double* zeta_disc, double* zeta_conn,
+                      int nthreads) {
+  Graph& gd = *(Graph*)g_dr;
+  Graph& gr = *(Graph*)g_r;
+  if (gd.nb != gr.nb) return -1;
+  const int nb = gd.nb;
+  Conf4* conf = conf4_cached(nb);
+  const size_t nc = conf->reps.size();
+  std::vector<uint64_t> pc(nb);
+  std::vector<double> nn(nb), rr(nb);
+  int st = or_pairs(g_dr, w_signed, pc.data(), nn.data());
+  if (!st) st = or_pairs(g_r, w_r, pc.data(), rr.data());
+  if (st) return st;
+  std::vector<uint64_t> e(nc);
+  std::vector<int64_t> o(nc);
+  std::vector<double> ne(nc), no(nc), re(nc), ro(nc);
+  st = or_count_4pcf(g_dr, w_signed, e.data(), o.data(), ne.data(), no.data(), nthreads);
+  if (!st) st = or_count_4pcf(g_r, w_r, e.data(), o.data(), re.data(), ro.data(), nthreads);
+  if (st) return st;
+  std::vector<double> x(nb);
+  for (int b = 0; b < nb; ++b) {
+    x[b] = nn[b] / rr[b];
+    if (xi) xi[b] = x[b];
+  }
+  for (size_t c = 0; c < nc; ++c) {
+    const Tup6& r = conf->reps[c];
+    volatile double t1 = x[r[0]] * x[r[5]];
+    volatile double t2 = x[r[1]] * x[r[4]];
+    volatile double t3 = x[r[2]] * x[r[3]];
+    volatile double s12 = t1 + t2;
+    const double disc = s12 + t3;
+    const double ze = ne[c] / re[c];
+    if (zeta_even) zeta_even[c] = ze;
+    if (zeta_odd) zeta_odd[c] = no[c] / re[c];
+    if (zeta_disc) zeta_disc[c] = disc;
+    if (zeta_conn) {
+      volatile double zc = ze - disc;
+      zeta_conn[c] = zc;
+    }
+  }
+  return 0;
+}
+
 }  // extern "C"
