@@ -72,8 +72,10 @@ typedef struct {
    * instead of staging them. 4 = gs_count_3pcf looks configuration indices
    * up in a shared table instead of computing them. 8 = gs_count_3pcf
    * limits its direct-address table to 2 KB (rows split at their largest id
-   * gap, or hashed). Results are identical; the bits exist for testing and
-   * tuning. */
+   * gap, or hashed). 16 = gs_count_3pcf gives each block's first staging
+   * wait no polls, so the call fails with GS_ETIMEOUT after the blocks have
+   * let their copies land (tests of the failure path). Other results are
+   * identical; the bits exist for testing and tuning. */
   int32_t variant;
   /* cudaStream_t for all device work; NULL = legacy default stream. */
   void* stream;
@@ -276,6 +278,41 @@ int gs_count_4pcf_parity(const gs_graph* g, const float* w, uint64_t* even, int6
  */
 int gs_disconnected_4pcf(const gs_graph* g, const float* w, const double* rr, uint64_t* pairs,
                          double* xi, double* zeta_disc, const gs_options* options);
+
+/*
+ * gs_connected_4pcf - connected 4pCF with the signed-weight estimator
+ * (Sec. 2.1 weights, Sec. 3.3, Eq. disc, Eq. conn). One weighted pair
+ * sweep and one weighted parity 4pCF pass over each of two graphs built on
+ * the same bin edges:
+ *   g_dr      graph of the union of data and randoms.
+ *   w_signed  float32 [n of g_dr], in g_dr's input order: data weights
+ *             (normalised by the caller to sum +1) and random weights
+ *             (normalised to sum -1). The signed pair sum of a bin is then
+ *             the Landy-Szalay numerator DD - 2DR + RR.
+ *   g_r       graph of the randoms alone.
+ *   w_r       float32 [n of g_r]: the random weights with the sign of a
+ *             data weight (normalised to sum +1); they give RR and RRRR.
+ * Outputs (each NULL or float64, host or device memory):
+ *   xi         [nb]       signed pair sum / RR (no constant subtracted).
+ *   zeta_even  [n_orbits] signed quadruplet sum / RRRR, even channel.
+ *   zeta_odd   [n_orbits] signed parity-odd quadruplet sum / RRRR.
+ *   zeta_disc  [n_orbits] xi(r01) xi(r23) + xi(r02) xi(r13) + xi(r03) xi(r12)
+ *              on each orbit representative.
+ *   zeta_conn  [n_orbits] zeta_even - zeta_disc; the odd channel is
+ *              connected as it stands and is not corrected.
+ * All sums are exact fixed-point sums rounded once to FP64; every ratio,
+ * product and sum above is one IEEE-rounded FP64 operation, left to right,
+ * without fused multiply-add. A bin or orbit with RR or RRRR zero yields
+ * the IEEE quotient (inf or NaN).
+ * Errors: GS_EINVAL (a NULL graph or weight array, different bin edges,
+ * options->shards > 1: ratios do not add over hub shards), GS_ERANGE
+ * (nb > 16), GS_EUNSUPPORTED (non-finite weights, or weights of one graph
+ * whose nonzero magnitudes span more than the exact fixed-point range,
+ * about a factor 2^5), GS_ENOMEM, GS_ETIMEOUT, GS_ECUDA.
+ */
+int gs_connected_4pcf(const gs_graph* g_dr, const float* w_signed, const gs_graph* g_r,
+                      const float* w_r, double* xi, double* zeta_even, double* zeta_odd,
+                      double* zeta_disc, double* zeta_conn, const gs_options* options);
 
 /* gs_num_configs - number of configurations: npoint 3 -> C(nb+2,3);
  * npoint 4 -> (nb^6 + 9 nb^4 + 14 nb^2) / 24 (Sec. 5.1, Sec. 5.2).

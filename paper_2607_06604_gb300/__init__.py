@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
     "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_4pcf",
-    "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_num_configs", "gs_config_bins",
+    "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
 ]
 
@@ -92,6 +92,7 @@ def _load():
         "gs_plan_destroy": ([P], None),
         "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
+        "gs_connected_4pcf": ([P, P, P, P, P, P, P, P, P, OP], ci),
         "gs_num_configs": ([ci, ci, ctypes.POINTER(i64)], ci),
         "gs_config_bins": ([ci, ci, i64, P, ctypes.POINTER(ci)], ci),
         "gs_free_graph": ([P], None),
@@ -343,6 +344,26 @@ def gs_disconnected_4pcf(g: Graph, w=None, rr=None, like=None, zeta=True, **opts
     _check(_lib.gs_disconnected_4pcf(g.handle, _ptr(w), _ptr(rr), _ptr(pairs), _ptr(xi), _ptr(z),
                                      ctypes.byref(o)), "gs_disconnected_4pcf")
     return pairs, xi, z
+
+
+def gs_connected_4pcf(g_dr: Graph, w_signed, g_r: Graph, w_r, **opts):
+    """Signed-weight connected 4pCF: dict of xi [nb] and zeta_even, zeta_odd,
+    zeta_disc, zeta_conn [n_orbits] (host NumPy, or torch tensors on the
+    weights' device when the weights are torch tensors)."""
+    if not _is_torch(w_signed):
+        w_signed = np.ascontiguousarray(w_signed, dtype=np.float32)
+    if not _is_torch(w_r):
+        w_r = np.ascontiguousarray(w_r, dtype=np.float32)
+    no = gs_num_configs(4, g_dr.nb)
+    out = {"xi": _empty_like_input(w_signed, (g_dr.nb,), np.float64)}
+    for k in ("zeta_even", "zeta_odd", "zeta_disc", "zeta_conn"):
+        out[k] = _empty_like_input(w_signed, (no,), np.float64)
+    o = _options(**opts)
+    _check(_lib.gs_connected_4pcf(g_dr.handle, _ptr(w_signed), g_r.handle, _ptr(w_r),
+                                  _ptr(out["xi"]), _ptr(out["zeta_even"]), _ptr(out["zeta_odd"]),
+                                  _ptr(out["zeta_disc"]), _ptr(out["zeta_conn"]), ctypes.byref(o)),
+           "gs_connected_4pcf")
+    return out
 
 
 class gs_server:

@@ -796,4 +796,49 @@ int gs_disconnected_4pcf(const gs_graph* G, const float* w, const double* rr, ui
   return st;
 }
 
+int gs_connected_4pcf(const gs_graph* G_dr, const float* w_signed, const gs_graph* G_r,
+                      const float* w_r, double* xi, double* zeta_even, double* zeta_odd,
+                      double* zeta_disc, double* zeta_conn, const gs_options* options) {
+  if (!G_dr || !G_r || !w_signed || !w_r) return GS_EINVAL;
+  const Graph& gdr = G_dr->g;
+  const Graph& gr = G_r->g;
+  if (gdr.nb != gr.nb) return GS_EINVAL;
+  if (gdr.edges != gr.edges) return GS_EINVAL;  // both graphs on the same bins
+  const Opts o = read_opts(options);
+  if (o.shards > 1) return GS_EINVAL;  // the ratios do not add over hub shards
+  int64_t no = 0;
+  int st = gs_num_configs(4, gdr.nb, &no);
+  if (st) return st;
+  {
+    Scratch sc(o.stream);
+    FixedW fdr, fr;
+    st = prepare_weights(gdr, w_signed, &fdr, sc, o.stream);
+    if (!st) st = prepare_weights(gr, w_r, &fr, sc, o.stream);
+    if (st) return st;
+    auto dev_out = [&](double* p, int64_t n) -> double* {
+      return !p ? nullptr : (is_device_ptr(p) ? p : sc.alloc<double>(n));
+    };
+    double* dx = dev_out(xi, gdr.nb);
+    double* de = dev_out(zeta_even, no);
+    double* dod = dev_out(zeta_odd, no);
+    double* dd = dev_out(zeta_disc, no);
+    double* dc = dev_out(zeta_conn, no);
+    if ((xi && !dx) || (zeta_even && !de) || (zeta_odd && !dod) || (zeta_disc && !dd) ||
+        (zeta_conn && !dc))
+      return GS_ENOMEM;
+    st = connected_device(gdr, fdr, gr, fr, dx, de, dod, dd, dc, o, sc);
+    OutBuf outs[5] = {{xi, dx, sizeof(double) * gdr.nb},
+                      {zeta_even, de, sizeof(double) * no},
+                      {zeta_odd, dod, sizeof(double) * no},
+                      {zeta_disc, dd, sizeof(double) * no},
+                      {zeta_conn, dc, sizeof(double) * no}};
+    for (auto& b : outs)
+      if (!st && b.user && b.dev != b.user)
+        st = cuda_status(cudaMemcpyAsync(b.user, b.dev, b.bytes, cudaMemcpyDeviceToHost, o.stream));
+    cudaError_t e = cudaStreamSynchronize(o.stream);
+    if (!st) st = cuda_status(e);
+  }
+  return st;
+}
+
 }  // extern "C"

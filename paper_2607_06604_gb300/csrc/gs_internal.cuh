@@ -166,6 +166,9 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
                   int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc);
 int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint64_t* d_pairs,
                       double* d_xi, double* d_zeta, const Opts& o, Scratch& sc);
+int connected_device(const Graph& gdr, const FixedW& fdr, const Graph& gr, const FixedW& fr,
+                     double* d_xi, double* d_even, double* d_odd, double* d_disc, double* d_conn,
+                     const Opts& o, Scratch& sc);
 int walk_words_device(Graph* g);
 int quantize_device(const double* d_pos, int64_t n, int64_t box_u, int periodic, int32_t* d_xyz,
                     cudaStream_t s, Scratch& sc);

@@ -6,7 +6,8 @@
 // The weighted pass walks rows (warp per hub) to pair w_i with w_j, in
 // exact fixed point. A single small kernel then forms RR, xi and
 // zeta_disc in FP64 with explicitly rounded operations (no contraction),
-// in the order the equation is written.
+// in the order the equation is written. The signed-weight estimator
+// (connected 4pCF) reuses the weighted sweep and the 4pCF kernel.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -126,6 +127,36 @@ __global__ void k_xi_disc(const unsigned long long* pairs, const double* wpairs_
 
 }  // namespace
 
+// Weighted pair sums of one graph: pairs[b] (counts), and on the device
+// wp_d[0..nb) = sum_{i<j in bin b} w_i w_j, wp_d[nb] = sum w_i,
+// wp_d[nb+1] = sum w_i^2, each the exact fixed-point sum rounded once.
+int pairs_weighted_device(const Graph& g, const FixedW& fw, unsigned long long* pairs,
+                          double* wp_d, const Opts& o, Scratch& sc, KernelTimer& timer) {
+  cudaStream_t s = o.stream;
+  const int nb = g.nb;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  unsigned long long* wacc = sc.alloc<unsigned long long>(3 * (size_t)nb + 6);
+  if (!wacc) return GS_ENOMEM;
+  cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * (3 * nb + 6), s);
+  timer.start(s);
+  int st = GS_OK;
+  if (g.n)
+    st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+      { k_pairs_weighted<<<sms * 8, kThreads, 0, s>>>(g.d_ptr, g.d_deg, v.adj, v.off1, v.split, v.off2,
+                                                    fw.d_W, v.h0, v.h1, nb, pairs, wacc,
+                                                    wacc + 3 * nb); note_launch(); }
+      return cuda_status(cudaGetLastError());
+    });
+  timer.stop(s);
+  if (st) return st;
+  { k_i192_to_double<<<1, 256, 0, s>>>(wacc, nb, 2 * fw.scale, wp_d); note_launch(); }
+  { k_i192_to_double<<<1, 32, 0, s>>>(wacc + 3 * nb, 1, fw.scale, wp_d + nb); note_launch(); }
+  { k_i192_to_double<<<1, 32, 0, s>>>(wacc + 3 * nb + 3, 1, 2 * fw.scale, wp_d + nb + 1); note_launch(); }
+  return cuda_status(cudaGetLastError());
+}
+
 int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint64_t* d_pairs,
                       double* d_xi, double* d_zeta, const Opts& o, Scratch& sc) {
   cudaStream_t s = o.stream;
@@ -147,23 +178,10 @@ int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint
   double* mom_d = nullptr;
   KernelTimer timer(o.kernel_ms);
   if (fw) {
-    unsigned long long* wacc = sc.alloc<unsigned long long>(3 * (size_t)nb + 6);
     wp_d = sc.alloc<double>(nb + 2);
-    if (!wacc || !wp_d) return GS_ENOMEM;
-    cudaMemsetAsync(wacc, 0, sizeof(unsigned long long) * (3 * nb + 6), s);
-    timer.start(s);
-    if (g.n)
-      st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
-        { k_pairs_weighted<<<sms * 8, kThreads, 0, s>>>(g.d_ptr, g.d_deg, v.adj, v.off1, v.split, v.off2,
-                                                      fw->d_W, v.h0, v.h1, nb, pairs, wacc,
-                                                      wacc + 3 * nb); note_launch(); }
-        return cuda_status(cudaGetLastError());
-      });
-    timer.stop(s);
+    if (!wp_d) return GS_ENOMEM;
+    st = pairs_weighted_device(g, *fw, pairs, wp_d, o, sc, timer);
     if (st) return st;
-    { k_i192_to_double<<<1, 256, 0, s>>>(wacc, nb, 2 * fw->scale, wp_d); note_launch(); }
-    { k_i192_to_double<<<1, 32, 0, s>>>(wacc + 3 * nb, 1, fw->scale, wp_d + nb); note_launch(); }
-    { k_i192_to_double<<<1, 32, 0, s>>>(wacc + 3 * nb + 3, 1, 2 * fw->scale, wp_d + nb + 1); note_launch(); }
     mom_d = wp_d + nb;
   } else if (g.slots) {
     timer.start(s);
@@ -187,6 +205,86 @@ int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
   timer.publish();
+  return cuda_status(cudaGetLastError());
+}
+
+// Signed-weight estimator (Sec. 3.3): with data weights summing to +1 and
+// random weights to -1 on the union, the signed pair sum is the
+// Landy-Szalay numerator and xi = signed pair sum / RR needs no constant;
+// zeta = signed quadruplet sum / RRRR per channel, and Eq. conn removes the
+// disconnected part (Eq. disc, from this xi) from the even channel only.
+// Every division and product is a single IEEE-rounded FP64 operation,
+// left to right, no contraction.
+__global__ void k_connected(const double* nn, const double* rr, const double* ne,
+                            const double* no, const double* re, int nb, const uint8_t* reps,
+                            int64_t n_orbits, double* xi_out, double* zeta_even,
+                            double* zeta_odd, double* zeta_disc, double* zeta_conn) {
+  __shared__ double xi[kMaxBins + 1];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    xi[b] = __ddiv_rn(nn[b], rr[b]);
+    if (xi_out) xi_out[b] = xi[b];
+  }
+  __syncthreads();
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_orbits;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t* r = reps + 6 * o;  // slots 01 02 03 12 13 23
+    const double t1 = __dmul_rn(xi[r[0]], xi[r[5]]);
+    const double t2 = __dmul_rn(xi[r[1]], xi[r[4]]);
+    const double t3 = __dmul_rn(xi[r[2]], xi[r[3]]);
+    const double disc = __dadd_rn(__dadd_rn(t1, t2), t3);
+    const double ze = __ddiv_rn(ne[o], re[o]);
+    if (zeta_even) zeta_even[o] = ze;
+    if (zeta_odd) zeta_odd[o] = __ddiv_rn(no[o], re[o]);
+    if (zeta_disc) zeta_disc[o] = disc;
+    if (zeta_conn) zeta_conn[o] = __dsub_rn(ze, disc);
+  }
+}
+
+int connected_device(const Graph& gdr, const FixedW& fdr, const Graph& gr, const FixedW& fr,
+                     double* d_xi, double* d_even, double* d_odd, double* d_disc, double* d_conn,
+                     const Opts& o, Scratch& sc) {
+  cudaStream_t s = o.stream;
+  const int nb = gdr.nb;
+  int st = GS_OK;
+  const Conf4Tables* t = conf4_tables(nb, &st);
+  if (!t) return st;
+  const int64_t no = t->n_orbits;
+  unsigned long long* pairs = sc.alloc<unsigned long long>(2 * (size_t)nb);
+  double* nn = sc.alloc<double>(nb + 2);
+  double* rr = sc.alloc<double>(nb + 2);
+  uint64_t* cnt = sc.alloc<uint64_t>(no);
+  int64_t* odd = sc.alloc<int64_t>(no);
+  double* ne = sc.alloc<double>(no);
+  double* nodd = sc.alloc<double>(no);
+  double* re = sc.alloc<double>(no);
+  if (!pairs || !nn || !rr || !cnt || !odd || !ne || !nodd || !re) return GS_ENOMEM;
+  cudaMemsetAsync(pairs, 0, sizeof(unsigned long long) * 2 * nb, s);
+  // each pass reports its own kernel time; the call reports their sum
+  double ms[4] = {0.0, 0.0, 0.0, 0.0};
+  Opts sub = o;
+  {
+    KernelTimer timer(o.kernel_ms ? ms : nullptr);
+    st = pairs_weighted_device(gdr, fdr, pairs, nn, o, sc, timer);
+    if (!st) st = pairs_weighted_device(gr, fr, pairs + nb, rr, o, sc, timer);
+    if (!st) st = cuda_status(cudaStreamSynchronize(s));
+    if (st) return st;
+    timer.publish();
+  }
+  sub.kernel_ms = o.kernel_ms ? ms + 1 : nullptr;
+  st = count4_device(gdr, &fdr, true, cnt, odd, ne, nodd, sub, sc);
+  if (st) return st;
+  sub.kernel_ms = o.kernel_ms ? ms + 2 : nullptr;
+  st = count4_device(gr, &fr, false, cnt, nullptr, re, nullptr, sub, sc);
+  if (st) return st;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (int)std::min<int64_t>(sms, (no + 255) / 256);
+  { k_connected<<<std::max(blocks, 1), 256, 0, s>>>(nn, rr, ne, nodd, re, nb, t->d_reps, no, d_xi, d_even,
+                                                  d_odd, d_disc, d_conn); note_launch(); }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (o.kernel_ms) *o.kernel_ms = ms[0] + ms[1] + ms[2];
   return cuda_status(cudaGetLastError());
 }
 

@@ -345,6 +345,79 @@ def test_disconnected_parity(gs, torch_mod, weighted):
     np.testing.assert_allclose(z2, rz2, rtol=RTOL, atol=RTOL)
 
 
+def connected_case(periodic, seed):
+    """Clustered data and uniform randoms (twice as many) in one box, with
+    data weights normalised to +1 and random weights to -1 (Sec. 3.3)."""
+    L = 110.0
+    box_u = int(L * 1024)
+    D = oracle.quantize(catalogs.neyman_scott(4000, L, seed=seed, sigma=1.5, periodic=periodic),
+                        box_u, periodic)
+    R = oracle.quantize(catalogs.uniform(8000, L, seed=seed + 1), box_u, periodic)
+    wd = catalogs.uniform_weights(len(D), seed=seed + 2).astype(np.float64)
+    wr = catalogs.uniform_weights(len(R), seed=seed + 3).astype(np.float64)
+    w_signed = np.concatenate([wd / wd.sum(), -wr / wr.sum()]).astype(np.float32)
+    w_r = (wr / wr.sum()).astype(np.float32)
+    U = np.concatenate([D, R])
+    edges = catalogs.bin_edges_u(0.0, 11.0, 4)
+    return U, R, (box_u if periodic else 0), edges, w_signed, w_r
+
+
+def assert_estimator_close(got, want):
+    """Both sides round exact sums once; every later step is one IEEE op, so
+    the results agree to a few ulps of the operands' scale (conn subtracts
+    two nearly equal terms, hence the scale |even| + |disc|)."""
+    for k in ("xi", "zeta_even", "zeta_odd", "zeta_disc"):
+        a, b = np.asarray(got[k]), want[k]
+        assert np.array_equal(np.isnan(a), np.isnan(b)), k
+        m = ~np.isnan(b)
+        np.testing.assert_allclose(a[m], b[m], rtol=RTOL, atol=0, err_msg=k)
+    scale = np.abs(want["zeta_even"]) + np.abs(want["zeta_disc"])
+    m = ~np.isnan(scale)
+    assert np.all(np.abs(np.asarray(got["zeta_conn"])[m] - want["zeta_conn"][m]) <= RTOL * scale[m])
+
+
+@pytest.mark.parametrize("periodic,seed", [(True, 91), (False, 93)])
+def test_connected_4pcf_signed_estimator(gs, torch_mod, periodic, seed):
+    U, R, bu, edges, w_signed, w_r = connected_case(periodic, seed)
+    want = oracle.connected_4pcf(oracle.Graph(U, bu, edges), w_signed,
+                                 oracle.Graph(R, bu, edges), w_r)
+    assert np.isfinite(want["zeta_even"]).sum() > 20 and np.abs(want["zeta_odd"]).sum() > 0
+    # host arrays in, host arrays out
+    got = gs.gs_connected_4pcf(gs.gs_build_graph(U, bu, edges), w_signed,
+                               gs.gs_build_graph(R, bu, edges), w_r)
+    assert_estimator_close(got, want)
+    # device arrays, and an out-of-core union graph (three windows)
+    gd = gs.gs_build_graph(dev(torch_mod, U), bu, edges, force_windows=3)
+    got_d = gs.gs_connected_4pcf(gd, dev(torch_mod, w_signed),
+                                 gs.gs_build_graph(dev(torch_mod, R), bu, edges),
+                                 dev(torch_mod, w_r))
+    for k in got:
+        assert got_d[k].is_cuda
+        assert np.array_equal(got_d[k].cpu().numpy(), got[k], equal_nan=True), k
+
+
+def test_connected_4pcf_errors(gs, torch_mod):
+    U, R, bu, edges, w_signed, w_r = connected_case(True, 95)
+    gd = gs.gs_build_graph(U[:2000], bu, edges)
+    e_other = edges.copy()
+    e_other[-1] -= 1
+    gr_other = gs.gs_build_graph(R[:1000], bu, e_other)
+    with pytest.raises(gs.GSError) as e:
+        gs.gs_connected_4pcf(gd, w_signed[:2000], gr_other, w_r[:1000])
+    assert e.value.status == -1
+    gr = gs.gs_build_graph(R[:1000], bu, edges)
+    with pytest.raises(gs.GSError) as e:
+        gs.gs_connected_4pcf(gd, w_signed[:2000], gr, w_r[:1000], shards=2)
+    assert e.value.status == -1
+    wide = w_signed[:2000].copy()
+    wide[0] = 1e6  # magnitudes beyond the exact fixed-point range
+    with pytest.raises(gs.GSError) as e:
+        gs.gs_connected_4pcf(gd, wide, gr, w_r[:1000])
+    assert e.value.status == -6
+    out = gs.gs_connected_4pcf(gd, w_signed[:2000], gr, w_r[:1000])
+    assert out["xi"].shape == (len(edges) - 1,)
+
+
 # ----------------------------------------------------------------------------
 # Full-size workloads
 
@@ -430,3 +503,21 @@ def test_full_size_out_of_core_workload(gs, torch_mod):
     Xmd = dev(torch_mod, Xm)
     cm = gs.gs_count_3pcf(gs.gs_build_graph(Xmd, 0, edges), like=Xmd).cpu().numpy()
     assert np.array_equal(cm, c0)
+
+
+def test_expired_wait_reports_timeout_and_context_survives(gs, torch_mod):
+    """A bounded device wait that runs out (variant 16 gives the first
+    staging wait no polls) makes the call return GS_ETIMEOUT without a
+    fault; the next calls on the same graph and device succeed."""
+    box_u = 60_000
+    X = rand_lattice(8000, box_u, 81)
+    edges = np.array([0, 3000, 6000], dtype=np.int64)
+    g = gs.gs_build_graph(X, box_u, edges)
+    ref = gs.gs_count_3pcf(g)
+    for _ in range(2):
+        with pytest.raises(gs.GSError) as e:
+            gs.gs_count_3pcf(g, variant=16)
+        assert e.value.status == -5
+        assert np.array_equal(gs.gs_count_3pcf(g), ref)
+    torch_mod.cuda.synchronize()
+    assert np.array_equal(oracle.Graph(X, box_u, edges).count_3pcf(), ref)
