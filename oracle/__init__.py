@@ -204,3 +204,140 @@ def connected_4pcf(g_dr: Graph, w_signed, g_r: Graph, w_r):
     if st != 0:
         raise ValueError(f"oracle connected 4pCF failed ({st})")
     return out
+
+
+# ----------------------------------------------------------------------------
+# Configuration tooling (post-processing of the binned counts)
+
+def _det_exact(M):
+    """Determinant by the Leibniz sum over permutations, in exact arithmetic
+    (ints or Fractions): fine for the 5 x 5 Cayley-Menger matrix."""
+    import itertools
+    n = len(M)
+    total = 0
+    for p in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if p[i] > p[j])
+        t = -1 if inv & 1 else 1
+        for i in range(n):
+            t = t * M[i][p[i]]
+        total += t
+    return total
+
+
+_SLOTS = ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))
+
+
+def cayley_menger_det(d2):
+    """Cayley-Menger determinant of four points from their six squared
+    distances in slot order (01, 02, 03, 12, 13, 23): the 5 x 5 matrix with
+    a zero corner, a border of ones and the squared distances. It equals
+    288 V^2 for a tetrahedron of volume V, and is not positive when the six
+    lengths cannot be realised in three dimensions (Sec. 5.2, Cayley-Menger
+    criterion)."""
+    D = [[0] * 4 for _ in range(4)]
+    for (i, j), x in zip(_SLOTS, d2):
+        D[i][j] = D[j][i] = x
+    M = [[0, 1, 1, 1, 1]] + [[1] + D[i] for i in range(4)]
+    return _det_exact(M)
+
+
+def config_mask_cm(nb: int, edges_u):
+    """uint8 [n_orbits]: 1 when the orbit's six bin centres (midpoints of the
+    bin edges, exact rationals) give a positive Cayley-Menger determinant."""
+    from fractions import Fraction
+    e = [int(x) for x in edges_u]
+    centre = [Fraction(e[b] + e[b + 1], 2) for b in range(nb)]
+    no = num_configs(4, nb)
+    mask = np.zeros(no, dtype=np.uint8)
+    for o in range(no):
+        bins, _ = config_bins(4, nb, o)
+        mask[o] = 1 if cayley_menger_det([centre[b] ** 2 for b in bins]) > 0 else 0
+    return mask
+
+
+def _perm_parity(p):
+    return sum(1 for i in range(len(p)) for j in range(i + 1, len(p)) if p[i] > p[j]) & 1
+
+
+def _relabel(t, p):
+    """Tuple in slot order after vertex v takes the label p[v]."""
+    d = {}
+    for (i, j), x in zip(_SLOTS, t):
+        a, b = sorted((p[i], p[j]))
+        d[(a, b)] = x
+    return tuple(d[s] for s in _SLOTS)
+
+
+def _orbit_index(nb: int):
+    """Every labelling of every orbit representative -> (orbit, parity of
+    the relabelling, or None when both parities reach it)."""
+    import itertools
+    out = {}
+    for o in range(num_configs(4, nb)):
+        rep, _ = config_bins(4, nb, o)
+        seen = {}
+        for p in itertools.permutations(range(4)):
+            t = _relabel(rep, p)
+            par = _perm_parity(p)
+            if t in seen and seen[t] != par:
+                seen[t] = None
+            elif t not in seen:
+                seen[t] = par
+        for t, par in seen.items():
+            out[t] = (o, par)
+    return out
+
+
+def rebin_3pcf(nb_fine: int, nb_coarse: int, bin_map, counts, wsum=None):
+    """Fine 3pCF counts -> coarse: each fine configuration's bins go through
+    bin_map (fine bin -> coarse bin, or -1 to drop the configuration), are
+    sorted and ranked among the coarse configurations (Sec. 5.1 combines
+    caps after rebinning fine bins exactly). Weighted sums add in ascending
+    fine index."""
+    idx = {config_bins(3, nb_coarse, c)[0]: c for c in range(num_configs(3, nb_coarse))}
+    out = np.zeros(num_configs(3, nb_coarse), dtype=np.uint64)
+    wout = None if wsum is None else np.zeros(len(out), dtype=np.float64)
+    for f in range(num_configs(3, nb_fine)):
+        bins, _ = config_bins(3, nb_fine, f)
+        m = [int(bin_map[b]) for b in bins]
+        if min(m) < 0:
+            continue
+        c = idx[tuple(sorted(m))]
+        out[c] += np.uint64(counts[f])
+        if wout is not None:
+            wout[c] = wout[c] + float(wsum[f])
+    return out if wout is None else (out, wout)
+
+
+def rebin_4pcf(nb_fine: int, nb_coarse: int, bin_map, even, odd=None, weven=None, wodd=None):
+    """Fine 4pCF orbits -> coarse orbits. The fine representative's bins go
+    through bin_map (a -1 drops it) in the fine representative's vertex
+    labelling; the coarse orbit holding that labelled tuple is found, and
+    odd counts change sign when the relabelling onto the coarse
+    representative is an odd permutation (Sec. 3.2: the handedness of V
+    follows the vertex order). Coarse orbits that are not chiral keep no odd
+    part. Sums add in ascending fine index."""
+    index = _orbit_index(nb_coarse)
+    nc = num_configs(4, nb_coarse)
+    chiral = [config_bins(4, nb_coarse, c)[1] for c in range(nc)]
+    e_out = np.zeros(nc, dtype=np.uint64)
+    o_out = np.zeros(nc, dtype=np.int64)
+    we_out = np.zeros(nc) if weven is not None else None
+    wo_out = np.zeros(nc) if wodd is not None else None
+    for f in range(num_configs(4, nb_fine)):
+        bins, _ = config_bins(4, nb_fine, f)
+        m = tuple(int(bin_map[b]) for b in bins)
+        if min(m) < 0:
+            continue
+        c, par = index[m]
+        e_out[c] += np.uint64(even[f])
+        if we_out is not None:
+            we_out[c] = we_out[c] + float(weven[f])
+        if not chiral[c]:
+            continue
+        s = -1 if par else 1
+        if odd is not None:
+            o_out[c] += s * int(odd[f])
+        if wo_out is not None:
+            wo_out[c] = wo_out[c] + s * float(wodd[f])
+    return e_out, o_out, we_out, wo_out

@@ -2,7 +2,7 @@
 
 The query path needs no collective on its data path: ranks either count
 independent catalogues (a mock ensemble) or disjoint hub shards of one
-catalogue (gs_options.shard / shards, Sec. 4.5's hub-window decomposition).
+catalogue (gs_options.shard / shards, the hub-window decomposition of Sec. 4.7).
 The only exchanges are these reductions of finished results.
 """
 from __future__ import annotations

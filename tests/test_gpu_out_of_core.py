@@ -2,7 +2,7 @@
 device budget keeps them in pinned host memory and every query streams
 hub windows with their halo rows. Results must be bit-identical to the
 resident graph for every window count (the paper validated all kernels in
-single-pass and chunked modes, Sec. 4.7)."""
+single-pass and chunked modes, Sec. 4.8)."""
 import numpy as np
 import pytest
 

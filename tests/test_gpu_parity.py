@@ -301,7 +301,7 @@ def test_4pcf_global_workspace(gs, torch_mod, periodic):
 
 @pytest.mark.parametrize("mirrored_fraction", [0.0, 0.3, 0.5])
 def test_parity_injection_gpu(gs, torch_mod, mirrored_fraction):
-    """Sec. 4.6 injection test: odd = N_L - N_R exactly at the injected orbit."""
+    """Sec. 4.9 injection test: odd = N_L - N_R exactly at the injected orbit."""
     gold = json.load(open(os.path.join(GOLDEN, "injection_tetrahedron.json")))
     edges = np.array(gold["edges_u"], dtype=np.int64)
     n = gold["n_struct"]

@@ -38,7 +38,7 @@ def test_signed_pair_sum_is_the_landy_szalay_numerator():
 
 
 def test_connected_injection_count_level():
-    """Sec. 4.6 with the signed-weight estimator: isolated chiral tetrahedra
+    """Sec. 4.9 with the signed-weight estimator: isolated chiral tetrahedra
     as data, randoms in a cube farther than r_max from every structure. No
     quadruplet mixes the two, so the signed odd sum at the injected orbit is
     w_D^4 (N_L - N_R) plus w_R^4 times the randoms' own odd count, and the

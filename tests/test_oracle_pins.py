@@ -217,7 +217,7 @@ def test_parity_mirror_rotation_relabel():
 
 @pytest.mark.parametrize("mirrored_fraction", [0.0, 0.3, 0.5])
 def test_parity_injection(mirrored_fraction):
-    """Sec. 4.6: isolated chiral tetrahedra give odd = N_L - N_R exactly."""
+    """Sec. 4.9: isolated chiral tetrahedra give odd = N_L - N_R exactly."""
     gold = load_golden("injection_tetrahedron.json")
     edges_u = np.array(gold["edges_u"], dtype=np.int64)
     n = gold["n_struct"]
