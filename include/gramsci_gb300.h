@@ -314,6 +314,58 @@ int gs_connected_4pcf(const gs_graph* g_dr, const float* w_signed, const gs_grap
                       const float* w_r, double* xi, double* zeta_even, double* zeta_odd,
                       double* zeta_disc, double* zeta_conn, const gs_options* options);
 
+/*
+ * gs_config_mask_cm - Cayley-Menger realisability of the 4pCF orbits
+ * (Sec. 5.2): an orbit is kept when the six bin centres of its
+ * representative, taken as edge lengths, give a positive Cayley-Menger
+ * determinant (288 V^2 > 0), i.e. form a non-degenerate tetrahedron.
+ *   nb         1..16 bins; edges_u int64 [nb+1] host, strictly increasing,
+ *              edges_u[0] >= 0, edges_u[nb] <= 2^19 (512 h^-1Mpc).
+ *   mask       uint8 [n_orbits] (host or device): 1 kept, 0 excluded.
+ *   n_realisable  NULL or receives the number kept.
+ * The bin centre is the midpoint (E_b + E_{b+1}) / 2; the determinant's sign
+ * is evaluated exactly (128-bit integers on doubled centres).
+ * Errors: GS_EINVAL, GS_ERANGE, GS_ENOMEM, GS_ECUDA.
+ */
+int gs_config_mask_cm(int nb, const int64_t* edges_u, uint8_t* mask, int64_t* n_realisable,
+                      const gs_options* options);
+
+/*
+ * gs_rebin_3pcf - exact fine-to-coarse rebinning of 3pCF results (Sec. 5.1
+ * rebins the native fine-bin measurement onto coarser bins).
+ *   bin_map    int32 [nb_fine] (host or device): the coarse bin holding each
+ *              fine bin, or -1 to drop every configuration using that fine
+ *              bin. Coarse bins that unite consecutive fine bins give exactly
+ *              the counts a direct count on the coarse edges gives.
+ *   counts     NULL or uint64 [C(nb_fine+2,3)] -> coarse_counts uint64
+ *              [C(nb_coarse+2,3)] (both NULL or both set).
+ *   wsum       NULL or float64 fine -> coarse_wsum float64 coarse.
+ * Each coarse configuration sums its fine configurations in ascending fine
+ * index (integers exactly, FP64 with one rounding per addition), so results
+ * repeat bit for bit. Inputs and outputs may be host or device memory.
+ * Errors: GS_EINVAL (NULL map, unpaired arrays, a map value outside
+ * [-1, nb_coarse)), GS_ERANGE (nb > 254), GS_ENOMEM, GS_ECUDA.
+ */
+int gs_rebin_3pcf(int nb_fine, int nb_coarse, const int32_t* bin_map, const uint64_t* counts,
+                  const double* wsum, uint64_t* coarse_counts, double* coarse_wsum,
+                  const gs_options* options);
+
+/*
+ * gs_rebin_4pcf - exact fine-to-coarse rebinning of parity 4pCF results.
+ * A fine orbit's representative goes through bin_map in its own vertex
+ * labelling and lands in the coarse orbit holding that labelled tuple. Its
+ * odd count changes sign when the relabelling onto the coarse representative
+ * is an odd permutation (the sign of V follows the vertex order, Sec. 3.2),
+ * and is dropped when the coarse orbit is not chiral.
+ *   even/c_even uint64, odd/c_odd int64, weven/c_weven and wodd/c_wodd
+ *   float64, fine [n_orbits(nb_fine)] -> coarse [n_orbits(nb_coarse)];
+ *   each pair both NULL or both set. Summation order as gs_rebin_3pcf.
+ * Errors: as gs_rebin_3pcf; GS_ERANGE when a bin count exceeds 16.
+ */
+int gs_rebin_4pcf(int nb_fine, int nb_coarse, const int32_t* bin_map, const uint64_t* even,
+                  const int64_t* odd, const double* weven, const double* wodd, uint64_t* c_even,
+                  int64_t* c_odd, double* c_weven, double* c_wodd, const gs_options* options);
+
 /* gs_num_configs - number of configurations: npoint 3 -> C(nb+2,3);
  * npoint 4 -> (nb^6 + 9 nb^4 + 14 nb^2) / 24 (Sec. 5.1, Sec. 5.2).
  * Errors: GS_EINVAL (npoint not 3 or 4, nb < 1), GS_ERANGE (npoint 4 with

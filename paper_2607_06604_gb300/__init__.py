@@ -23,7 +23,8 @@ from . import build as _build
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
     "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_4pcf",
-    "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_num_configs", "gs_config_bins",
+    "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_config_mask_cm",
+    "gs_rebin_3pcf", "gs_rebin_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
 ]
 
@@ -93,6 +94,9 @@ def _load():
         "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
         "gs_connected_4pcf": ([P, P, P, P, P, P, P, P, P, OP], ci),
+        "gs_config_mask_cm": ([ci, P, P, ctypes.POINTER(i64), OP], ci),
+        "gs_rebin_3pcf": ([ci, ci, P, P, P, P, P, OP], ci),
+        "gs_rebin_4pcf": ([ci, ci, P, P, P, P, P, P, P, P, P, OP], ci),
         "gs_num_configs": ([ci, ci, ctypes.POINTER(i64)], ci),
         "gs_config_bins": ([ci, ci, i64, P, ctypes.POINTER(ci)], ci),
         "gs_free_graph": ([P], None),
@@ -364,6 +368,52 @@ def gs_connected_4pcf(g_dr: Graph, w_signed, g_r: Graph, w_r, **opts):
                                   _ptr(out["zeta_disc"]), _ptr(out["zeta_conn"]), ctypes.byref(o)),
            "gs_connected_4pcf")
     return out
+
+
+def gs_config_mask_cm(nb: int, edges_u, **opts):
+    """(uint8 mask [n_orbits], number kept): orbits whose bin centres form a
+    tetrahedron by the Cayley-Menger criterion."""
+    edges = np.ascontiguousarray(edges_u, dtype=np.int64)
+    mask = np.empty(gs_num_configs(4, nb), np.uint8)
+    kept = ctypes.c_int64(0)
+    o = _options(**opts)
+    _check(_lib.gs_config_mask_cm(int(nb), _ptr(edges), _ptr(mask), ctypes.byref(kept),
+                                  ctypes.byref(o)), "gs_config_mask_cm")
+    return mask, int(kept.value)
+
+
+def _rebin_in(x, dtype):
+    return None if x is None else (x if _is_torch(x) else np.ascontiguousarray(x, dtype=dtype))
+
+
+def gs_rebin_3pcf(nb_fine: int, nb_coarse: int, bin_map, counts=None, wsum=None, **opts):
+    """Coarse (counts, wsum) from fine ones; either may be None."""
+    bm = _rebin_in(bin_map, np.int32)
+    counts, wsum = _rebin_in(counts, np.uint64), _rebin_in(wsum, np.float64)
+    ref = counts if counts is not None else wsum
+    nc = gs_num_configs(3, nb_coarse)
+    oc = None if counts is None else _empty_like_input(ref, (nc,), np.uint64)
+    ow = None if wsum is None else _empty_like_input(ref, (nc,), np.float64)
+    o = _options(**opts)
+    _check(_lib.gs_rebin_3pcf(int(nb_fine), int(nb_coarse), _ptr(bm), _ptr(counts), _ptr(wsum),
+                              _ptr(oc), _ptr(ow), ctypes.byref(o)), "gs_rebin_3pcf")
+    return oc, ow
+
+
+def gs_rebin_4pcf(nb_fine: int, nb_coarse: int, bin_map, even=None, odd=None, weven=None,
+                  wodd=None, **opts):
+    """Coarse (even, odd, weven, wodd) from fine ones; any may be None."""
+    bm = _rebin_in(bin_map, np.int32)
+    ins = [_rebin_in(even, np.uint64), _rebin_in(odd, np.int64), _rebin_in(weven, np.float64),
+           _rebin_in(wodd, np.float64)]
+    ref = next((x for x in ins if x is not None), None)
+    nc = gs_num_configs(4, nb_coarse)
+    outs = [None if x is None else _empty_like_input(ref, (nc,), dt)
+            for x, dt in zip(ins, (np.uint64, np.int64, np.float64, np.float64))]
+    o = _options(**opts)
+    _check(_lib.gs_rebin_4pcf(int(nb_fine), int(nb_coarse), _ptr(bm), *[_ptr(x) for x in ins],
+                              *[_ptr(x) for x in outs], ctypes.byref(o)), "gs_rebin_4pcf")
+    return tuple(outs)
 
 
 class gs_server:
