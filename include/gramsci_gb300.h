@@ -237,6 +237,22 @@ int gs_plan_wait(gs_plan* plan, void* stream);
 void gs_plan_destroy(gs_plan* plan);
 
 /*
+ * gs_count_3pcf_equilateral - equilateral 3pCF (named among the GPU query
+ * kernels in Sec. 3.5 and Sec. 4.8; the paper gives no definition). Here it
+ * is the nb configurations whose three sides share one bin: counts[b] is the
+ * number of triangles with all three pair separations in bin b, equal to the
+ * full 3pCF's entry at configuration (b, b, b), computed by a kernel that
+ * follows same-bin edges only.
+ *   w       NULL or float32 [n] weights (caller's order).
+ *   counts  uint64 [nb]; wsum NULL or float64 [nb] (exact sums of
+ *           w_i w_j w_k rounded once; needs w).
+ * Host or device pointers; options->shard/shards split the hubs as for
+ * gs_count_3pcf. Errors: as gs_count_3pcf.
+ */
+int gs_count_3pcf_equilateral(const gs_graph* g, const float* w, uint64_t* counts, double* wsum,
+                              const gs_options* options);
+
+/*
  * gs_count_4pcf - binned tetrahedron counts (Sec. 2.2, Sec. 3.1.1):
  * tetrahedra whose six pairs are all edges, one count per S4 orbit.
  *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact).

@@ -341,3 +341,15 @@ def rebin_4pcf(nb_fine: int, nb_coarse: int, bin_map, even, odd=None, weven=None
         if wo_out is not None:
             wo_out[c] = wo_out[c] + s * float(wodd[f])
     return e_out, o_out, we_out, wo_out
+
+
+def equilateral_3pcf(g: Graph, w=None):
+    """Equilateral 3pCF read as the configurations (b, b, b): triangles with
+    all three sides in bin b (the paper names the kernel without defining
+    it). Counts uint64 [nb] (and weighted sums f64 [nb] with w), taken from
+    the full 3pCF."""
+    r = g.count_3pcf(w)
+    c, ws = (r if w is not None else (r, None))
+    idx = {config_bins(3, g.nb, k)[0]: k for k in range(num_configs(3, g.nb))}
+    sel = [idx[(b, b, b)] for b in range(g.nb)]
+    return (c[sel], ws[sel]) if w is not None else c[sel]

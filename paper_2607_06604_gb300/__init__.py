@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
-    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_4pcf",
+    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_3pcf_equilateral", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_config_mask_cm",
     "gs_rebin_3pcf", "gs_rebin_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
@@ -94,6 +94,7 @@ def _load():
         "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
         "gs_connected_4pcf": ([P, P, P, P, P, P, P, P, P, OP], ci),
+        "gs_count_3pcf_equilateral": ([P, P, P, P, OP], ci),
         "gs_config_mask_cm": ([ci, P, P, ctypes.POINTER(i64), OP], ci),
         "gs_rebin_3pcf": ([ci, ci, P, P, P, P, P, OP], ci),
         "gs_rebin_4pcf": ([ci, ci, P, P, P, P, P, P, P, P, P, OP], ci),
@@ -368,6 +369,18 @@ def gs_connected_4pcf(g_dr: Graph, w_signed, g_r: Graph, w_r, **opts):
                                   _ptr(out["zeta_disc"]), _ptr(out["zeta_conn"]), ctypes.byref(o)),
            "gs_connected_4pcf")
     return out
+
+
+def gs_count_3pcf_equilateral(g: Graph, w=None, like=None, **opts):
+    """Triangles with all three sides in bin b, for each b (uint64 [nb]), and
+    with w the exact weighted sums (float64 [nb])."""
+    ref = like if like is not None else w
+    counts = _empty_like_input(ref, (g.nb,), np.uint64)
+    wsum = _empty_like_input(ref, (g.nb,), np.float64) if w is not None else None
+    o = _options(**opts)
+    _check(_lib.gs_count_3pcf_equilateral(g.handle, _ptr(w), _ptr(counts), _ptr(wsum),
+                                          ctypes.byref(o)), "gs_count_3pcf_equilateral")
+    return (counts, wsum) if w is not None else counts
 
 
 def gs_config_mask_cm(nb: int, edges_u, **opts):

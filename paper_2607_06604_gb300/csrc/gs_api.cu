@@ -796,6 +796,33 @@ int gs_disconnected_4pcf(const gs_graph* G, const float* w, const double* rr, ui
   return st;
 }
 
+int gs_count_3pcf_equilateral(const gs_graph* G, const float* w, uint64_t* counts, double* wsum,
+                              const gs_options* options) {
+  if (!G || !counts || (wsum && !w)) return GS_EINVAL;
+  const Graph& g = G->g;
+  const Opts o = read_opts(options);
+  int st = GS_OK;
+  {
+    Scratch sc(o.stream);
+    FixedW fw;
+    if (w) {
+      st = prepare_weights(g, w, &fw, sc, o.stream);
+      if (st) return st;
+    }
+    uint64_t* dc = is_device_ptr(counts) ? counts : sc.alloc<uint64_t>(g.nb);
+    double* dw = wsum ? (is_device_ptr(wsum) ? wsum : sc.alloc<double>(g.nb)) : nullptr;
+    if (!dc || (wsum && !dw)) return GS_ENOMEM;
+    st = equi3_device(g, w ? &fw : nullptr, dc, dw, o, sc);
+    OutBuf outs[2] = {{counts, dc, sizeof(uint64_t) * g.nb}, {wsum, dw, sizeof(double) * g.nb}};
+    for (auto& b : outs)
+      if (!st && b.user && b.dev != b.user)
+        st = cuda_status(cudaMemcpyAsync(b.user, b.dev, b.bytes, cudaMemcpyDeviceToHost, o.stream));
+    cudaError_t e = cudaStreamSynchronize(o.stream);
+    if (!st) st = cuda_status(e);
+  }
+  return st;
+}
+
 int gs_connected_4pcf(const gs_graph* G_dr, const float* w_signed, const gs_graph* G_r,
                       const float* w_r, double* xi, double* zeta_even, double* zeta_odd,
                       double* zeta_disc, double* zeta_conn, const gs_options* options) {

@@ -169,6 +169,8 @@ int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint
 int connected_device(const Graph& gdr, const FixedW& fdr, const Graph& gr, const FixedW& fr,
                      double* d_xi, double* d_even, double* d_odd, double* d_disc, double* d_conn,
                      const Opts& o, Scratch& sc);
+int equi3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
+                 const Opts& o, Scratch& sc);
 int walk_words_device(Graph* g);
 int quantize_device(const double* d_pos, int64_t n, int64_t box_u, int periodic, int32_t* d_xyz,
                     cudaStream_t s, Scratch& sc);

@@ -122,3 +122,54 @@ def test_rebin_errors(gs):
     with pytest.raises(gs.GSError) as e:
         gs.gs_rebin_4pcf(17, 2, np.zeros(17, np.int32), np.zeros(1, np.uint64))
     assert e.value.status == -2
+
+
+def diagonal(nb):
+    idx = {oracle.config_bins(3, nb, k)[0]: k for k in range(oracle.num_configs(3, nb))}
+    return [idx[(b, b, b)] for b in range(nb)]
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_equilateral_matches_oracle_and_full_3pcf(gs, periodic):
+    L = 150.0
+    box_u = int(L * 1024)
+    X = oracle.quantize(catalogs.neyman_scott(40_000, L, seed=321, sigma=2.0, periodic=periodic),
+                        box_u, periodic)
+    w = catalogs.uniform_weights(len(X), seed=322)
+    edges = catalogs.bin_edges_u(0.0, 10.0, 7)
+    bu = box_u if periodic else 0
+    c, ws = oracle.equilateral_3pcf(oracle.Graph(X, bu, edges), w)
+    g = gs.gs_build_graph(X, bu, edges)
+    gc, gw = gs.gs_count_3pcf_equilateral(g, w)
+    assert c.sum() > 100_000
+    assert np.array_equal(gc, c)
+    np.testing.assert_allclose(gw, ws, rtol=1e-12)
+    fc, fw = gs.gs_count_3pcf(g, w)
+    sel = diagonal(len(edges) - 1)
+    assert np.array_equal(gc, fc[sel]) and np.array_equal(gw, fw[sel])
+    assert np.array_equal(gs.gs_count_3pcf_equilateral(g), c)
+    # out-of-core windows and hub shards
+    g3 = gs.gs_build_graph(X, bu, edges, force_windows=3)
+    c3, w3 = gs.gs_count_3pcf_equilateral(g3, w)
+    assert np.array_equal(c3, gc) and np.array_equal(w3, gw)
+    cs = sum(gs.gs_count_3pcf_equilateral(g, shard=k, shards=2).astype(np.int64) for k in range(2))
+    assert np.array_equal(cs, gc.astype(np.int64))
+
+
+def test_equilateral_long_rows(gs):
+    """A dense clump gives hub rows longer than the staged capacity (4096
+    words), which are searched in global memory."""
+    import torch
+    rng = np.random.default_rng(331)
+    box_u = 200_000
+    X = np.concatenate([rng.integers(90_000, 94_000, size=(4600, 3)),
+                        rng.integers(0, box_u, size=(20_000, 3))]).astype(np.int32)
+    edges = np.array([0, 2500, 4500, 7000], dtype=np.int64)
+    g = gs.gs_build_graph(X, box_u, edges)
+    assert gs.gs_graph_info(g)["max_degree"] > 4096
+    fc = gs.gs_count_3pcf(g)
+    gc = gs.gs_count_3pcf_equilateral(g)
+    assert np.array_equal(gc, fc[diagonal(3)]) and gc.sum() > 0
+    Xd = torch.from_numpy(X).cuda()
+    gd = gs.gs_count_3pcf_equilateral(gs.gs_build_graph(Xd, box_u, edges), like=Xd)
+    assert gd.is_cuda and np.array_equal(gd.cpu().numpy(), gc)

@@ -117,3 +117,26 @@ def test_rebin_identity_map():
     n3 = oracle.num_configs(3, nb)
     c3 = rng.integers(0, 1000, n3).astype(np.uint64)
     assert np.array_equal(oracle.rebin_3pcf(nb, nb, np.arange(nb), c3), c3)
+
+
+def test_equilateral_brute_force():
+    """All triples of a tiny catalogue: triangles whose three pair bins agree."""
+    import itertools
+
+    from tests import bruteforce
+    rng = np.random.default_rng(17)
+    box_u = 20_000
+    X = rng.integers(0, box_u, size=(90, 3)).astype(np.int32)
+    w = catalogs.uniform_weights(len(X), seed=18)
+    edges = np.array([0, 2000, 3500, 5000], dtype=np.int64)
+    B = bruteforce.bin_matrix(X, box_u, edges)
+    want = np.zeros(3, np.uint64)
+    wsum = np.zeros(3)
+    for i, j, k in itertools.combinations(range(len(X)), 3):
+        if B[i, j] >= 0 and B[i, j] == B[i, k] == B[j, k]:
+            want[B[i, j]] += 1
+            wsum[B[i, j]] += float(w[i]) * float(w[j]) * float(w[k])
+    c, ws = oracle.equilateral_3pcf(oracle.Graph(X, box_u, edges), w)
+    assert want.sum() > 20
+    assert np.array_equal(c, want)
+    np.testing.assert_allclose(ws, wsum, rtol=1e-12)
