@@ -51,8 +51,11 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-4pcf", action="store_true",
                     help="skip the secondary 4pCF + parity measurement")
-    ap.add_argument("--profile", choices=["count3", "count3w", "count4", "pairs"], default=None,
+    ap.add_argument("--profile", choices=["count3", "count3w", "count4", "pairs", "equi3w"],
+                    default=None,
                     help="run one small case of one kernel for an ncu capture (no JSON)")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the connected 4pCF, equilateral and tooling measurements")
     ap.add_argument("--mocks", type=int, default=0,
                     help="also serve this many lognormal mock catalogues (request loop)")
     ap.add_argument("--mock-nmax", type=float, default=4e5)
@@ -357,6 +360,7 @@ def run_ours(args):
     quad = None
     if not args.no_4pcf:
         quad = measure_4pcf(gs, torch)
+    nxt = None if args.no_next else measure_next(gs, torch, dev[1], box_u, edges, k_ms)
     mocks = measure_mocks(gs, torch, args.mocks, args.mock_nmax) if args.mocks else None
     ooc = measure_ooc(gs, torch) if args.ooc else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -374,7 +378,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "quadruplets": quad,
-            "mocks": mocks, "out_of_core": ooc,
+            "mocks": mocks, "out_of_core": ooc, "next_rows": nxt,
             "graph_randoms": {k2: info[k2] for k2 in ("edges", "max_degree", "probe_words",
                                                       "walk_words", "edge_slots")}}
     print(json.dumps(line), flush=True)
@@ -411,6 +415,71 @@ def measure_4pcf(gs, torch, runs=2):
             "call_ms": best, "kernel_ms": km.value, "pair_sweep_ms": pk.value,
             "pair_sweep_gbs": info["edge_slots"] * 4 / (pk.value / 1e3) / 1e9 if pk.value else None,
             "odd_abs_sum": float(odd.abs().sum().item())}
+
+
+def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
+    """The rows beyond the core path, each timed with CUDA events after one
+    warm-up call: the equilateral 3pCF on the randoms' graph of the default
+    workload (beside the full 3pCF kernel time), the signed-weight connected
+    4pCF on 1e5 data + 1e5 randoms, and the configuration tooling."""
+    import ctypes
+
+    def timed(fn):
+        fn()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        out = fn()
+        t1.record()
+        torch.cuda.synchronize()
+        return out, t0.elapsed_time(t1)
+
+    out = {}
+    pos, w = randoms
+    g = gs.gs_build_graph(gs.gs_quantize(pos, box_u, True), box_u, edges)
+    info = gs.gs_graph_info(g)
+    km = ctypes.c_double(0.0)
+    (c, _), ms = timed(lambda: gs.gs_count_3pcf_equilateral(g, w, kernel_ms=km))
+    words = info["edges"] + info["probe_words"]
+    out["equilateral"] = {
+        "workload": "3e6 uniform randoms, L=1000, rmax 40, 20 bins, weighted",
+        "call_ms": ms, "kernel_ms": km.value, "triangles": float(c.sum().item()),
+        "full_3pcf_kernel_ms": count3_ms,
+        "alg_bytes_per_launch": 4 * words,
+        "achieved_gbs": 4 * words / (km.value / 1e3) / 1e9 if km.value else None}
+    g.close()
+
+    spec = catalogs.draw("ns100k_r100k_L400_r30_nb8")
+    bu, e4 = spec["box_u"], spec["edges_u"]
+    R = catalogs.uniform(spec["randoms"], spec["box"], spec["random_seed"])
+    wd = catalogs.uniform_weights(spec["n"], seed=spec["weight_seed"]).astype(np.float64)
+    wr = catalogs.uniform_weights(spec["randoms"], seed=spec["weight_seed"] + 1).astype(np.float64)
+    ws = np.concatenate([wd / wd.sum(), -wr / wr.sum()]).astype(np.float32)
+    wr1 = (wr / wr.sum()).astype(np.float32)
+    U = torch.from_numpy(np.concatenate([spec["pos"], R])).cuda()
+    gdr = gs.gs_build_graph(gs.gs_quantize(U, bu, True), bu, e4)
+    gr = gs.gs_build_graph(gs.gs_quantize(torch.from_numpy(R).cuda(), bu, True), bu, e4)
+    wsd, wrd = torch.from_numpy(ws).cuda(), torch.from_numpy(wr1).cuda()
+    kc = ctypes.c_double(0.0)
+    res, ms = timed(lambda: gs.gs_connected_4pcf(gdr, wsd, gr, wrd, kernel_ms=kc))
+    tet = float(gs.gs_count_4pcf(gdr).sum()) + float(gs.gs_count_4pcf(gr).sum())
+    out["connected_4pcf"] = {
+        "workload": "ns100k_r100k_L400_r30_nb8", "call_ms": ms, "kernel_ms": kc.value,
+        "tetrahedra": tet, "quadruplets_per_s": tet / (ms / 1e3),
+        "finite_orbits": int(torch.isfinite(res["zeta_conn"]).sum().item())}
+    gdr.close()
+    gr.close()
+
+    edges16 = np.array([int(20 * 1024 + b * 2.8125 * 1024) for b in range(17)], dtype=np.int64)
+    (mask, kept), ms_cm = timed(lambda: gs.gs_config_mask_cm(16, edges16))
+    n16 = gs.gs_num_configs(4, 16)
+    rng = np.random.default_rng(0)
+    ev = torch.from_numpy(rng.integers(0, 1 << 30, n16).astype(np.uint64)).cuda()
+    bmap = torch.from_numpy((np.arange(16) // 2).astype(np.int32)).cuda()
+    _, ms_rb = timed(lambda: gs.gs_rebin_4pcf(16, 8, bmap, ev))
+    out["tooling"] = {"cm_mask_nb16_ms": ms_cm, "orbits": n16, "realisable": kept,
+                      "rebin_4pcf_16_to_8_ms": ms_rb}
+    return out
 
 
 def make_mocks(count, nmax, seed=11):
@@ -532,7 +601,7 @@ def run_profile(args):
 
     import paper_2607_06604_gb300 as gs
     torch.cuda.set_device(0)
-    if args.profile in ("count3", "count3w", "pairs"):
+    if args.profile in ("count3", "count3w", "pairs", "equi3w"):
         # 1e6 uniform points at the randoms' density (3e-3 per (h^-1 Mpc)^3),
         # rmax 40 in 20 bins: a 1.6 GB graph
         L = 693.0
@@ -546,6 +615,8 @@ def run_profile(args):
                 gs.gs_count_3pcf(g, like=pos)
             elif args.profile == "count3w":
                 gs.gs_count_3pcf(g, w)
+            elif args.profile == "equi3w":
+                gs.gs_count_3pcf_equilateral(g, w)
             else:
                 gs.gs_disconnected_4pcf(g, like=pos, zeta=False)
     else:

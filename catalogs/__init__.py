@@ -178,6 +178,11 @@ WORKLOADS = {
     # 2e5 Neyman-Scott points, periodic L=400, rmax 30 in 8 bins (4pCF + parity)
     "ns200k_L400_r30_nb8": dict(kind="neyman_scott", n=200_000, box=400.0, periodic=True,
                                 rmin=0.0, rmax=30.0, nb=8, seed=4, sigma=2.0),
+    # 1e5 Neyman-Scott data + 1e5 uniform randoms (1:1), periodic L=400, rmax 30 in 8
+    # bins: the connected 4pCF with signed weights
+    "ns100k_r100k_L400_r30_nb8": dict(kind="neyman_scott", n=100_000, box=400.0, periodic=True,
+                                      rmin=0.0, rmax=30.0, nb=8, seed=6, sigma=2.0,
+                                      randoms=100_000, random_seed=7, weight_seed=8),
     # 1e6 Neyman-Scott (sigma 5), open box L=1494, rmax 150 in 15 bins (out-of-core)
     "ns1M_open_L1494_r150_nb15": dict(kind="neyman_scott", n=1_000_000, box=1494.0,
                                       periodic=False, rmin=0.0, rmax=150.0, nb=15, seed=5,
