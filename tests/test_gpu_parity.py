@@ -381,7 +381,8 @@ def test_connected_4pcf_signed_estimator(gs, torch_mod, periodic, seed):
     U, R, bu, edges, w_signed, w_r = connected_case(periodic, seed)
     want = oracle.connected_4pcf(oracle.Graph(U, bu, edges), w_signed,
                                  oracle.Graph(R, bu, edges), w_r)
-    assert np.isfinite(want["zeta_even"]).sum() > 20 and np.abs(want["zeta_odd"]).sum() > 0
+    assert np.isfinite(want["zeta_even"]).sum() > 20
+    assert np.nansum(np.abs(want["zeta_odd"])) > 0  # empty RRRR bins give NaN
     # host arrays in, host arrays out
     got = gs.gs_connected_4pcf(gs.gs_build_graph(U, bu, edges), w_signed,
                                gs.gs_build_graph(R, bu, edges), w_r)
