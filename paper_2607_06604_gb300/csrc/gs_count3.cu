@@ -73,7 +73,8 @@ struct Smem {
   int64_t* wst;        // weighted: stage_alloc staged weights of N+(i) (8 bytes each)
   uint16_t* lut;       // nb^3 configuration indices (or nullptr)
   unsigned* hist;      // nconf
-  unsigned long long* whist;  // 2 nconf (lo, hi) words
+  unsigned long long* whist;  // 2 nconf (lo, hi) words: the CTA's 128-bit sums
+  unsigned* hacc;      // 3 nconf: the current hub's 96-bit sums of W_j W_k (lo, mid, hi)
 };
 
 __device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int nb) {
@@ -87,15 +88,35 @@ enum : int { kNone = 0, kExact = 2 };
 template <int WM>
 using WType = int64_t;
 
+// One triangle. With shared histograms the weight argument is W_j (the
+// spoke's own weight): W_j W_k (|.| < 2^60) is added to the hub's 96-bit
+// accumulator with 32-bit shared atomics only (64-bit shared atomics cost
+// about 3.5 times as much on GB300), and fold_hub multiplies the hub's sums
+// by W_i once per hub. With global histograms it is W_i W_j and the
+// 128-bit product goes straight to the 192-bit global sums.
 template <int WM, bool SMEM_HIST>
-__device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Wij, WType<WM> Wk) {
+__device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Wsp, WType<WM> Wk) {
   if (SMEM_HIST) atomicAdd(sm.hist + cf, 1u);
   else atomicAdd(c.counts + cf, 1ull);
   if constexpr (WM == kExact) {
-    long long lo, hi;
-    mul_i128(Wij, Wk, &lo, &hi);
-    if (SMEM_HIST) atomic_add_i128(sm.whist + 2 * cf, lo, hi);
-    else atomic_add_i192(c.wacc + 3 * cf, (unsigned long long)lo, (unsigned long long)hi);
+    if (SMEM_HIST) {
+      const long long x = Wsp * Wk;
+      const uint32_t x0 = (uint32_t)x;
+      const uint32_t x1 = (uint32_t)((unsigned long long)x >> 32);
+      const uint32_t o0 = atomicAdd(sm.hacc + 3 * cf, x0);
+      const uint32_t c0 = (o0 + x0 < o0) ? 1u : 0u;
+      const uint32_t a1 = x1 + c0;
+      uint32_t a2 = (x < 0 ? 0xFFFFFFFFu : 0u) + ((a1 < x1) ? 1u : 0u);
+      if (a1) {
+        const uint32_t o1 = atomicAdd(sm.hacc + 3 * cf + 1, a1);
+        a2 += (o1 + a1 < o1) ? 1u : 0u;
+      }
+      if (a2) atomicAdd(sm.hacc + 3 * cf + 2, a2);
+    } else {
+      long long lo, hi;
+      mul_i128(Wsp, Wk, &lo, &hi);
+      atomic_add_i192(c.wacc + 3 * cf, (unsigned long long)lo, (unsigned long long)hi);
+    }
   }
 }
 
@@ -125,6 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     sm.hist = reinterpret_cast<unsigned*>(p);
     p += ((a.nconf * 4 + 15) / 16) * 16;
     sm.whist = reinterpret_cast<unsigned long long*>(p);
+    sm.hacc = reinterpret_cast<unsigned*>(sm.whist + 2 * a.nconf);
   }
   __shared__ uint64_t bar;
   __shared__ int64_t s_hub;
@@ -145,6 +167,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     for (int k = tid; k < a.nconf; k += kThreads) sm.hist[k] = 0;
     if (WEIGHTED)
       for (int k = tid; k < (WM == kExact ? 2 : 1) * a.nconf; k += kThreads) sm.whist[k] = 0;
+    if (WM == kExact)
+      for (int k = tid; k < 3 * a.nconf; k += kThreads) sm.hacc[k] = 0;
   }
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -174,6 +198,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       }
     }
   };
+  // the hub's 96-bit sums S[k] of W_j W_k, times W_i, into the CTA's
+  // 128-bit sums (each thread owns its configurations; no atomics)
+  auto fold_hub = [&](int64_t Wi) {
+    if constexpr (SMEM_HIST && WM == kExact) {
+      for (int k = tid; k < a.nconf; k += kThreads) {
+        const uint32_t l = sm.hacc[3 * k], m = sm.hacc[3 * k + 1], h = sm.hacc[3 * k + 2];
+        if (!(l | m | h)) continue;
+        sm.hacc[3 * k] = sm.hacc[3 * k + 1] = sm.hacc[3 * k + 2] = 0u;
+        // S = (int32)h 2^64 + ml; S W_i as a 128-bit two's-complement value
+        const unsigned long long ml = ((unsigned long long)m << 32) | l;
+        const unsigned long long uw = (unsigned long long)Wi;
+        const unsigned long long plo = ml * uw;
+        unsigned long long phi = __umul64hi(ml, uw) - (Wi < 0 ? ml : 0ull);
+        phi += (unsigned long long)((long long)(int32_t)h * Wi);
+        const unsigned long long olo = sm.whist[2 * k];
+        const unsigned long long nlo = olo + plo;
+        sm.whist[2 * k] = nlo;
+        sm.whist[2 * k + 1] += phi + ((nlo < olo) ? 1ull : 0ull);
+      }
+    }
+  };
+
   // bounded wait on the bulk copy; false when it timed out (block-uniform)
   // On an expired wait the block reports it, then waits (bounded again) for
   // its own copy to land before giving up, so no copy outlives the block.
@@ -254,8 +300,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     const int64_t span = (int64_t)hub_hi - i;  // ids i+1 .. hub_hi
     const bool staged = d <= a.stage_cap;
     // weighted hubs need their row and weights staged (positions come from
-    // the bitmap rank); the bitmap + 16-bit prefix take 6 bytes per 32 ids
-    const int64_t table_span = WEIGHTED ? (int64_t)(a.span_cap / 6) * 32 : (int64_t)a.span_cap;
+    // the bitmap rank); each 32 ids take one 64-bit entry: the bitmap word
+    // and the rank of its first bit, read together by one shared load
+    const int64_t table_span = WEIGHTED ? (int64_t)(a.span_cap / 8) * 32 : (int64_t)a.span_cap;
     bool use_table = !a.force_hash && (!WEIGHTED || staged);
     // The table covers ids [i+1, near_hi] at offsets 0 .. len1-1 and, for
     // rows split at their largest id gap (wrap-around neighbours of a
@@ -314,20 +361,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       auto slot = [&](uint32_t key) -> uint32_t {
         return key <= near_hi ? key - base : key - far_lo + far_off;
       };
-      uint32_t* bm = reinterpret_cast<uint32_t*>(sm.table);
+      uint2* bm = reinterpret_cast<uint2*>(sm.table);  // (bits, rank of bit 0)
       const int nw = (int)((tspan + 31) >> 5);
-      uint16_t* pre = reinterpret_cast<uint16_t*>(bm + nw);
       if (WEIGHTED) {
         for (int k = tid; k < d; k += kThreads) {
           const uint32_t off = slot(edge_id(hr[k]));
-          atomicOr(bm + (off >> 5), 1u << (off & 31));
+          atomicOr(&bm[off >> 5].x, 1u << (off & 31));
         }
         __syncthreads();
         // exclusive prefix of the words' popcounts: the rank of every bit
         const int per = (nw + kThreads - 1) / kThreads;
         const int w0 = min(nw, tid * per), w1 = min(nw, w0 + per);
         int sum = 0;
-        for (int q = w0; q < w1; ++q) sum += __popc(bm[q]);
+        for (int q = w0; q < w1; ++q) sum += __popc(bm[q].x);
         int x = sum;
         for (int o = 1; o < 32; o <<= 1) {
           const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -346,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         __syncthreads();
         int run = x - sum + (warp ? s_warp_sum[warp - 1] : 0);
         for (int q = w0; q < w1; ++q) {
-          pre[q] = (uint16_t)run;
-          run += __popc(bm[q]);
+          bm[q].y = (uint32_t)run;
+          run += __popc(bm[q].x);
         }
       } else {
         for (int k = tid; k < d; k += kThreads) {
@@ -371,7 +417,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
         for (;;) {
           const int bij = (int)edge_bin(wij);
-          const WT Wij = Wi * (staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij)));
+          const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
+          const WT Wsp = SMEM_HIST ? Wj : Wi * Wj;
           const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
           const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
           uint4 vn = none;
@@ -405,18 +452,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
             off[q] = ok[q] ? slot(key) : 0u;
           }
           if (WEIGHTED) {
-            uint32_t bw[4];
+            uint2 bw[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) bw[q] = bm[off[q] >> 5];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const uint32_t bit = 1u << (off[q] & 31);
-              if (ok[q] && (bw[q] & bit)) {
-                const int pos = (int)pre[off[q] >> 5] + __popc(bw[q] & (bit - 1u));
+              if (ok[q] && (bw[q].x & bit)) {
+                const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
                 const WT packed = wst[pos];
                 record<WM, SMEM_HIST>(
                     sm, c, conf_index(sm, bij, (int)(packed & 0xFF), (int)edge_bin(vv[q]), nb),
-                    Wij, packed >> 8);
+                    Wsp, packed >> 8);
               }
             }
           } else {
@@ -443,10 +490,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         }
       }
       __syncthreads();
+      fold_hub(Wi);
       if (WEIGHTED) {
-        // the next hub's bitmap may extend over this hub's prefix words
-        for (int k = tid; k < d; k += kThreads) bm[slot(edge_id(hr[k])) >> 5] = 0u;
-        for (int q = tid; q < (nw + 1) / 2; q += kThreads) bm[nw + q] = 0u;
+        // ranks are rewritten for every word a hub uses; only bits need clearing
+        for (int k = tid; k < d; k += kThreads) bm[slot(edge_id(hr[k])) >> 5].x = 0u;
       } else {
         for (int k = tid; k < d; k += kThreads) sm.table[slot(edge_id(hr[k]))] = kAbsent;
       }
@@ -485,7 +532,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         const uint32_t j = edge_id(wij);
         if (j >= seg_hi) break;  // every k > j; none left in this segment
         const int bij = (int)edge_bin(wij);
-        const WT Wij = Wi * wget<WM>(c, j);
+        const WT Wj = wget<WM>(c, j);
+        const WT Wsp = SMEM_HIST ? Wj : Wi * Wj;
         const uint32_t* rj = row_at(c.adj, c.ptr, j, c.adj_off, c.split, c.adj_off2);
         const int dj4 = (int)pad_row(c.deg[j]);
         int start = 0;
@@ -514,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               if (e == kSentinel) break;
               if (edge_id(e) == key) {
                 record<WM, SMEM_HIST>(
-                    sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wij,
+                    sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wsp,
                     wget<WM>(c, key));
                 break;
               }
@@ -530,6 +578,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       for (int k = tid; k < T; k += kThreads) table[k] = idle;
       __syncthreads();
     }
+    fold_hub(Wi);
   }
   __syncthreads();
   flush();
@@ -545,7 +594,12 @@ struct Count3Launch {
   bool smem_hist = true;
 };
 
-Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut) {
+// Hubs with more than kMaxSmemHistDeg neighbours could overflow the 32-bit
+// shared counters within one hub; graphs with such rows count straight into
+// the global histograms.
+constexpr int kMaxSmemHistDeg = 65535;
+
+Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, int max_deg) {
   const bool weighted = wmode != kNone;
   // weighted launches stage rows and weights of up to 2048 neighbours
   int dev = 0, optin = 0;
@@ -554,12 +608,13 @@ Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut) {
   auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
   const size_t nb3 = (size_t)nb * nb * nb;
   const size_t lut = (use_lut && nb3 <= (size_t)kLutMax) ? pad16(nb3 * 2) : 0;
-  size_t hist = pad16((size_t)nconf * 4) + (size_t)nconf * (wmode == kExact ? 16 : 0);
+  // counts, then (weighted) the CTA's 128-bit sums and the hub's 96-bit sums
+  size_t hist = pad16((size_t)nconf * 4) + (wmode == kExact ? pad16((size_t)nconf * 28) : 0);
   Count3Launch L;
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
   const size_t stage_words = weighted ? 2048 : kStageCap;
   const size_t fixed = stage_words * (weighted ? 12 : 4) + lut;
-  L.smem_hist = fixed + hist + 32 * 1024 <= avail;
+  L.smem_hist = fixed + hist + 32 * 1024 <= avail && max_deg <= kMaxSmemHistDeg;
   if (!L.smem_hist) hist = 0;
   L.span_cap = (int)((avail - fixed - hist) & ~(size_t)15);
   L.stage_words = (int)stage_words;
@@ -657,7 +712,7 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
     return cuda_status(cudaGetLastError());
   }
 
-  const Count3Launch L = count3_launch(g.nb, nconf, wm, (o.variant & 4) != 0);
+  const Count3Launch L = count3_launch(g.nb, nconf, wm, (o.variant & 4) != 0, g.max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
@@ -754,7 +809,9 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
-  const Count3Launch L = count3_launch(nb, nconf, wm, (o.variant & 4) != 0);
+  int max_deg = 0;
+  for (int k = 0; k < ng; ++k) max_deg = std::max(max_deg, gr[k]->max_deg);
+  const Count3Launch L = count3_launch(nb, nconf, wm, (o.variant & 4) != 0, max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
@@ -898,7 +955,7 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
     a.hub_counter = counter;
     a.err = err;
-    const Count3Launch L = count3_launch(g.nb, nconf, kNone, (o.variant & 4) != 0);
+    const Count3Launch L = count3_launch(g.nb, nconf, kNone, (o.variant & 4) != 0, g.max_deg);
     a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
     a.stage_alloc = L.stage_words;
     a.use_lut = (o.variant & 4) ? 1 : 0;
@@ -994,7 +1051,9 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.hub_counter = P->counter;
   a.err = P->err;
-  const Count3Launch L = count3_launch(nb, nconf, kNone, (o.variant & 4) != 0);
+  int max_deg = 0;
+  for (int k = 0; k < n_graphs; ++k) max_deg = std::max(max_deg, graphs[k]->g.max_deg);
+  const Count3Launch L = count3_launch(nb, nconf, kNone, (o.variant & 4) != 0, max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 1 : 0;
