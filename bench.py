@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--profile", choices=["count3", "count3w", "count4", "pairs", "equi3w"],
                     default=None,
                     help="run one small case of one kernel for an ncu capture (no JSON)")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="launch variant bits for the --profile case (0 = the library default)")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the connected 4pCF, equilateral and tooling measurements")
     ap.add_argument("--mocks", type=int, default=0,
@@ -78,7 +80,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_VERSION = "k_count3.v9"  # bump when k_count3 changes; stale captures then report null
+KERNEL_VERSION = "k_count3.v10"  # bump when k_count3 changes; stale captures then report null
 
 
 def recorded_traffic():
@@ -341,8 +343,9 @@ def run_ours(args):
     traffic = recorded_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-            "limiter": "instruction issue (ncu: 79% of issue slots busy, L1/shared pipe 44%, "
-                       "L2 hit 98.9%, DRAM 0.08%): spoke rows are re-read from L2",
+            "limiter": "instruction issue (ncu: 79% of issue slots busy, integer ALU pipe 66%, "
+                       "L1/shared pipe 65%, L2 hit 98.9%, DRAM 0.09%): spoke rows are re-read "
+                       "from L2",
             "kernel": "k_count3 (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
             "triangles_per_launch": float(counts[1].sum().item())}
 
@@ -612,9 +615,9 @@ def run_profile(args):
         w = torch.from_numpy(catalogs.uniform_weights(1_000_000, seed=6)).cuda()
         for _ in range(2):
             if args.profile == "count3":
-                gs.gs_count_3pcf(g, like=pos)
+                gs.gs_count_3pcf(g, like=pos, variant=args.variant)
             elif args.profile == "count3w":
-                gs.gs_count_3pcf(g, w)
+                gs.gs_count_3pcf(g, w, variant=args.variant)
             elif args.profile == "equi3w":
                 gs.gs_count_3pcf_equilateral(g, w)
             else:

@@ -69,13 +69,14 @@ typedef struct {
    * paths on any input (gs_count_3pcf probes a hash of the hub row staged
    * in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
    * global memory). 2 = gs_count_3pcf reads hub rows from global memory
-   * instead of staging them. 4 = gs_count_3pcf looks configuration indices
-   * up in a shared table instead of computing them. 8 = gs_count_3pcf
+   * instead of staging them. 4 = gs_count_3pcf computes configuration
+   * indices instead of looking them up in a shared table. 8 = gs_count_3pcf
    * limits its direct-address table to 2 KB (rows split at their largest id
    * gap, or hashed). 16 = gs_count_3pcf gives each block's first staging
    * wait no polls, so the call fails with GS_ETIMEOUT after the blocks have
-   * let their copies land (tests of the failure path). Other results are
-   * identical; the bits exist for testing and tuning. */
+   * let their copies land (tests of the failure path). 32 = weighted
+   * gs_count_3pcf compacts each warp's hits before recording them. Other
+   * results are identical; the bits exist for testing and tuning. */
   int32_t variant;
   /* cudaStream_t for all device work; NULL = legacy default stream. */
   void* stream;

@@ -354,8 +354,9 @@ const Conf4Tables* conf4_tables(int nb, int* status) {
 // [emin, emax], W_i = w_i * 2^(24 - emin) is an integer of at most
 // 25 + (emax - emin) bits.
 namespace {
-__global__ void k_weight_exponents(const float* w, int64_t n, int* emin, int* emax, int* bad) {
-  int lo = 1 << 20, hi = -(1 << 20), b = 0;
+__global__ void k_weight_exponents(const float* w, int64_t n, int* emin, int* emax, int* bad,
+                                   int* neg) {
+  int lo = 1 << 20, hi = -(1 << 20), b = 0, ng = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float x = w[i];
@@ -363,6 +364,7 @@ __global__ void k_weight_exponents(const float* w, int64_t n, int* emin, int* em
       b = 1;
       continue;
     }
+    if (x < 0.0f) ng = 1;
     if (x == 0.0f) continue;
     int e;
     frexpf(x, &e);
@@ -373,11 +375,13 @@ __global__ void k_weight_exponents(const float* w, int64_t n, int* emin, int* em
     lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     b |= __shfl_xor_sync(0xffffffffu, b, o);
+    ng |= __shfl_xor_sync(0xffffffffu, ng, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicMin(emin, lo);
     atomicMax(emax, hi);
     if (b) atomicOr(bad, 1);
+    if (ng) atomicOr(neg, 1);
   }
 }
 
@@ -393,13 +397,13 @@ __global__ void k_weight_fixed(const float* w, const int4* xyzp, int64_t n, int 
 
 int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cudaStream_t s) {
   const float* dw = static_cast<const float*>(to_device(sc, w, sizeof(float) * g.n, s));
-  int* flags = sc.alloc<int>(3);
+  int* flags = sc.alloc<int>(4);
   int64_t* W = sc.alloc<int64_t>(g.n);
   if (!dw || !flags || !W) return GS_ENOMEM;
-  const int init[3] = {1 << 20, -(1 << 20), 0};
+  const int init[4] = {1 << 20, -(1 << 20), 0, 0};
   cudaMemcpyAsync(flags, init, sizeof(init), cudaMemcpyHostToDevice, s);
-  { k_weight_exponents<<<304, 256, 0, s>>>(dw, g.n, flags, flags + 1, flags + 2); note_launch(); }
-  int h[3];
+  { k_weight_exponents<<<304, 256, 0, s>>>(dw, g.n, flags, flags + 1, flags + 2, flags + 3); note_launch(); }
+  int h[4];
   cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -407,6 +411,7 @@ int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cu
   if (h[0] > h[1]) h[0] = h[1] = 0;  // all weights zero
   out->scale = 24 - h[0];
   out->bits = 25 + (h[1] - h[0]) + 1;
+  out->nonneg = h[3] == 0;
   if (out->bits > 31) return GS_EUNSUPPORTED;
   { k_weight_fixed<<<304, 256, 0, s>>>(dw, g.d_xyzp, g.n, out->scale, W); note_launch(); }
   out->d_W = W;

@@ -62,6 +62,7 @@ struct Args {
   int stage_cap;          // hub rows up to this many words are staged
   int stage_alloc;        // words of the staging buffer
   int use_lut;            // 1: configuration index from the shared table
+  int compact;            // 1: weighted hits compacted per warp before recording
   uint32_t first_wait_limit;  // polls allowed for a block's first staging wait
   unsigned long long* hub_counter;
   int* err;
@@ -71,6 +72,7 @@ struct Smem {
   uint8_t* table;      // span_cap bytes; the hash path reuses it as words
   uint32_t* stage;     // stage_alloc words
   int64_t* wst;        // weighted: stage_alloc staged weights of N+(i) (8 bytes each)
+  uint32_t* queue;     // weighted, compacting launches: 128 hits per warp (or nullptr)
   uint16_t* lut;       // nb^3 configuration indices (or nullptr)
   unsigned* hist;      // nconf
   unsigned long long* whist;  // 2 nconf (lo, hi) words: the CTA's 128-bit sums
@@ -81,10 +83,17 @@ __device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int 
   return sm.lut ? (int)sm.lut[(bij * nb + bik) * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
 }
 
+// The same with the table row of b_ij precomputed (lbase = b_ij nb^2).
+__device__ inline int conf_at(const Smem& sm, int lbase, int bij, int bik, int bjk, int nb) {
+  return sm.lut ? (int)sm.lut[lbase + bik * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
+}
+
 // Weight modes: kNone and kExact (fixed-point integers: exact 128-bit
 // products in shared 128-bit accumulators, 192-bit global sums; shared FP64
 // reductions measured slower than this on GB300).
-enum : int { kNone = 0, kExact = 2 };
+// kExactPos is kExact for weights known to be nonnegative (a cheaper carry
+// chain in the per-hub limbs).
+enum : int { kNone = 0, kExact = 2, kExactPos = 3 };
 template <int WM>
 using WType = int64_t;
 
@@ -98,20 +107,30 @@ template <int WM, bool SMEM_HIST>
 __device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Wsp, WType<WM> Wk) {
   if (SMEM_HIST) atomicAdd(sm.hist + cf, 1u);
   else atomicAdd(c.counts + cf, 1ull);
-  if constexpr (WM == kExact) {
+  if constexpr (WM >= kExact) {
     if (SMEM_HIST) {
-      const long long x = Wsp * Wk;
+      // |W| < 2^30, so the product is one 32 x 32 -> 64-bit multiply
+      const long long x = (long long)(int32_t)Wsp * (int32_t)Wk;
       const uint32_t x0 = (uint32_t)x;
       const uint32_t x1 = (uint32_t)((unsigned long long)x >> 32);
       const uint32_t o0 = atomicAdd(sm.hacc + 3 * cf, x0);
       const uint32_t c0 = (o0 + x0 < o0) ? 1u : 0u;
       const uint32_t a1 = x1 + c0;
-      uint32_t a2 = (x < 0 ? 0xFFFFFFFFu : 0u) + ((a1 < x1) ? 1u : 0u);
-      if (a1) {
-        const uint32_t o1 = atomicAdd(sm.hacc + 3 * cf + 1, a1);
-        a2 += (o1 + a1 < o1) ? 1u : 0u;
+      if constexpr (WM == kExactPos) {
+        // 0 <= x < 2^60: x1 + c0 cannot wrap and the top limb only takes
+        // the mid limb's carries
+        if (a1) {
+          const uint32_t o1 = atomicAdd(sm.hacc + 3 * cf + 1, a1);
+          if (o1 + a1 < o1) atomicAdd(sm.hacc + 3 * cf + 2, 1u);
+        }
+      } else {
+        uint32_t a2 = (x < 0 ? 0xFFFFFFFFu : 0u) + ((a1 < x1) ? 1u : 0u);
+        if (a1) {
+          const uint32_t o1 = atomicAdd(sm.hacc + 3 * cf + 1, a1);
+          a2 += (o1 + a1 < o1) ? 1u : 0u;
+        }
+        if (a2) atomicAdd(sm.hacc + 3 * cf + 2, a2);
       }
-      if (a2) atomicAdd(sm.hacc + 3 * cf + 2, a2);
     } else {
       long long lo, hi;
       mul_i128(Wsp, Wk, &lo, &hi);
@@ -122,7 +141,7 @@ __device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Ws
 
 template <int WM>
 __device__ inline WType<WM> wget(const Cat& c, int64_t k) {
-  if constexpr (WM == kExact) return c.W[k];
+  if constexpr (WM >= kExact) return c.W[k];
   else return 0;
 }
 
@@ -140,6 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     p += (size_t)a.stage_alloc * 4;
     sm.wst = reinterpret_cast<int64_t*>(p);
     if (WEIGHTED) p += (size_t)a.stage_alloc * 8;
+    sm.queue = (WEIGHTED && a.compact) ? reinterpret_cast<uint32_t*>(p) : nullptr;
+    if (WEIGHTED && a.compact) p += (size_t)kWarps * 128 * 4;
     const int nb3 = a.nb * a.nb * a.nb;
     sm.lut = (a.use_lut && nb3 <= kLutMax) ? reinterpret_cast<uint16_t*>(p) : nullptr;
     if (a.use_lut && nb3 <= kLutMax) p += ((nb3 * 2 + 15) / 16) * 16;
@@ -166,8 +187,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   if (SMEM_HIST) {
     for (int k = tid; k < a.nconf; k += kThreads) sm.hist[k] = 0;
     if (WEIGHTED)
-      for (int k = tid; k < (WM == kExact ? 2 : 1) * a.nconf; k += kThreads) sm.whist[k] = 0;
-    if (WM == kExact)
+      for (int k = tid; k < (WM >= kExact ? 2 : 1) * a.nconf; k += kThreads) sm.whist[k] = 0;
+    if (WM >= kExact)
       for (int k = tid; k < 3 * a.nconf; k += kThreads) sm.hacc[k] = 0;
   }
   if (tid == 0) {
@@ -189,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         atomicAdd(c.counts + k, (unsigned long long)v);
         sm.hist[k] = 0;
       }
-      if (WM == kExact) {
+      if (WM >= kExact) {
         const unsigned long long lo = sm.whist[2 * k], hi = sm.whist[2 * k + 1];
         if (lo | hi) {
           atomic_add_i192(c.wacc + 3 * k, lo, hi);
@@ -201,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   // the hub's 96-bit sums S[k] of W_j W_k, times W_i, into the CTA's
   // 128-bit sums (each thread owns its configurations; no atomics)
   auto fold_hub = [&](int64_t Wi) {
-    if constexpr (SMEM_HIST && WM == kExact) {
+    if constexpr (SMEM_HIST && WM >= kExact) {
       for (int k = tid; k < a.nconf; k += kThreads) {
         const uint32_t l = sm.hacc[3 * k], m = sm.hacc[3 * k + 1], h = sm.hacc[3 * k + 2];
         if (!(l | m | h)) continue;
@@ -406,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       // first chunk of the warp's next spoke, is loaded before the current
       // one is probed.
       const uint4 none = make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+      const bool split = far_lo <= hub_hi;  // two table ranges (block-uniform)
       int sp = 0;
       if (lane == 0) sp = atomicAdd(&s_next, 1);
       sp = __shfl_sync(0xffffffffu, sp, 0);
@@ -415,10 +437,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         int dj4 = (int)pad_row(c.deg[edge_id(wij)]);
         int t0 = 0;
         uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
-        for (;;) {
-          const int bij = (int)edge_bin(wij);
+        // per-spoke constants: b_ij, the spoke's weight factor, and the row of
+        // the configuration table that b_ij selects
+        int bij = (int)edge_bin(wij);
+        int lbase = bij * nb * nb;
+        WT Wsp = 0;
+        if (WEIGHTED) {
           const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
-          const WT Wsp = SMEM_HIST ? Wj : Wi * Wj;
+          Wsp = SMEM_HIST ? Wj : Wi * Wj;
+        }
+        uint32_t* wq = sm.queue ? sm.queue + warp * 128 : nullptr;
+        for (;;) {
           const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
           const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
           uint4 vn = none;
@@ -445,25 +474,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
           // slot 0 and are discarded
           bool ok[4];
           uint32_t off[4];
+          if (split) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t key = edge_id(vv[q]);
-            ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo);
-            off[q] = ok[q] ? slot(key) : 0u;
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t key = edge_id(vv[q]);
+              ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo);
+              off[q] = ok[q] ? slot(key) : 0u;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t key = edge_id(vv[q]);
+              ok[q] = key <= hub_hi;
+              off[q] = ok[q] ? key - base : 0u;
+            }
           }
           if (WEIGHTED) {
             uint2 bw[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) bw[q] = bm[off[q] >> 5];
+            if (wq) {
+              // compact the chunk's hits into the warp's queue, then record
+              // them one per lane (full lanes instead of four divergent passes)
+              int n = 0;
+              const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t bit = 1u << (off[q] & 31);
-              if (ok[q] && (bw[q].x & bit)) {
-                const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
-                const WT packed = wst[pos];
+              for (int q = 0; q < 4; ++q) {
+                const uint32_t bit = 1u << (off[q] & 31);
+                const bool hit = ok[q] && (bw[q].x & bit);
+                const uint32_t m = __ballot_sync(0xffffffffu, hit);
+                if (hit)
+                  wq[n + __popc(m & lt)] =
+                      (bw[q].y + (uint32_t)__popc(bw[q].x & (bit - 1u))) | (edge_bin(vv[q]) << 16);
+                n += __popc(m);
+              }
+              __syncwarp();
+              for (int r = lane; r < n; r += 32) {
+                const uint32_t e = wq[r];
+                const WT packed = wst[e & 0xFFFFu];
                 record<WM, SMEM_HIST>(
-                    sm, c, conf_index(sm, bij, (int)(packed & 0xFF), (int)edge_bin(vv[q]), nb),
-                    Wsp, packed >> 8);
+                    sm, c, conf_at(sm, lbase, bij, (int)(packed & 0xFF), (int)(e >> 16), nb), Wsp,
+                    packed >> 8);
+              }
+              __syncwarp();
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const uint32_t bit = 1u << (off[q] & 31);
+                if (ok[q] && (bw[q].x & bit)) {
+                  const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
+                  const WT packed = wst[pos];
+                  record<WM, SMEM_HIST>(
+                      sm, c,
+                      conf_at(sm, lbase, bij, (int)(packed & 0xFF), (int)edge_bin(vv[q]), nb),
+                      Wsp, packed >> 8);
+                }
               }
             }
           } else {
@@ -473,7 +538,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
               if (ok[q] && bik[q] != kAbsent)
-                record<WM, SMEM_HIST>(sm, c, conf_index(sm, bij, bik[q], (int)edge_bin(vv[q]), nb),
+                record<WM, SMEM_HIST>(sm, c,
+                                      conf_at(sm, lbase, bij, bik[q], (int)edge_bin(vv[q]), nb),
                                       WT(0), WT(0));
           }
           if (more) {
@@ -485,6 +551,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
             rj = nrj;
             dj4 = ndj4;
             t0 = 0;
+            bij = (int)edge_bin(wij);
+            lbase = bij * nb * nb;
+            if (WEIGHTED) {
+              const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
+              Wsp = SMEM_HIST ? Wj : Wi * Wj;
+            }
           }
           v = vn;
         }
@@ -599,7 +671,8 @@ struct Count3Launch {
 // the global histograms.
 constexpr int kMaxSmemHistDeg = 65535;
 
-Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, int max_deg) {
+Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, bool compact,
+                           int max_deg) {
   const bool weighted = wmode != kNone;
   // weighted launches stage rows and weights of up to 2048 neighbours
   int dev = 0, optin = 0;
@@ -609,11 +682,12 @@ Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, int max_d
   const size_t nb3 = (size_t)nb * nb * nb;
   const size_t lut = (use_lut && nb3 <= (size_t)kLutMax) ? pad16(nb3 * 2) : 0;
   // counts, then (weighted) the CTA's 128-bit sums and the hub's 96-bit sums
-  size_t hist = pad16((size_t)nconf * 4) + (wmode == kExact ? pad16((size_t)nconf * 28) : 0);
+  size_t hist = pad16((size_t)nconf * 4) + (wmode >= kExact ? pad16((size_t)nconf * 28) : 0);
   Count3Launch L;
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
   const size_t stage_words = weighted ? 2048 : kStageCap;
-  const size_t fixed = stage_words * (weighted ? 12 : 4) + lut;
+  const size_t queue = (weighted && compact) ? (size_t)kWarps * 128 * 4 : 0;
+  const size_t fixed = stage_words * (weighted ? 12 : 4) + queue + lut;
   L.smem_hist = fixed + hist + 32 * 1024 <= avail && max_deg <= kMaxSmemHistDeg;
   if (!L.smem_hist) hist = 0;
   L.span_cap = (int)((avail - fixed - hist) & ~(size_t)15);
@@ -712,16 +786,20 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
     return cuda_status(cudaGetLastError());
   }
 
-  const Count3Launch L = count3_launch(g.nb, nconf, wm, (o.variant & 4) != 0, g.max_deg);
+  const Count3Launch L =
+      count3_launch(g.nb, nconf, wm, !(o.variant & 4), (o.variant & 32) != 0, g.max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
-  a.use_lut = (o.variant & 4) ? 1 : 0;
+  a.use_lut = (o.variant & 4) ? 0 : 1;
+  a.compact = (o.variant & 32) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
-  if (wm == kExact) kern = smem_hist ? k_count3<kExact, true, false> : k_count3<kExact, false, false>;
+  if (wm == kExact)
+    kern = !smem_hist ? k_count3<kExact, false, false>
+           : fw->nonneg ? k_count3<kExactPos, true, false> : k_count3<kExact, true, false>;
   else kern = smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
@@ -811,16 +889,22 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   int max_deg = 0;
   for (int k = 0; k < ng; ++k) max_deg = std::max(max_deg, gr[k]->max_deg);
-  const Count3Launch L = count3_launch(nb, nconf, wm, (o.variant & 4) != 0, max_deg);
+  const Count3Launch L =
+      count3_launch(nb, nconf, wm, !(o.variant & 4), (o.variant & 32) != 0, max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
-  a.use_lut = (o.variant & 4) ? 1 : 0;
+  a.use_lut = (o.variant & 4) ? 0 : 1;
+  a.compact = (o.variant & 32) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
-  if (wm == kExact) kern = smem_hist ? k_count3<kExact, true, true> : k_count3<kExact, false, true>;
+  bool nonneg = true;
+  for (int k = 0; k < ng && fws; ++k) nonneg = nonneg && fws[k].nonneg;
+  if (wm == kExact)
+    kern = !smem_hist ? k_count3<kExact, false, true>
+           : nonneg ? k_count3<kExactPos, true, true> : k_count3<kExact, true, true>;
   else kern = smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
@@ -955,10 +1039,11 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
     a.hub_counter = counter;
     a.err = err;
-    const Count3Launch L = count3_launch(g.nb, nconf, kNone, (o.variant & 4) != 0, g.max_deg);
+    const Count3Launch L = count3_launch(g.nb, nconf, kNone, !(o.variant & 4), false, g.max_deg);
     a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
     a.stage_alloc = L.stage_words;
-    a.use_lut = (o.variant & 4) ? 1 : 0;
+    a.use_lut = (o.variant & 4) ? 0 : 1;
+    a.compact = 0;
     a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
     void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
@@ -1053,10 +1138,11 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.err = P->err;
   int max_deg = 0;
   for (int k = 0; k < n_graphs; ++k) max_deg = std::max(max_deg, graphs[k]->g.max_deg);
-  const Count3Launch L = count3_launch(nb, nconf, kNone, (o.variant & 4) != 0, max_deg);
+  const Count3Launch L = count3_launch(nb, nconf, kNone, !(o.variant & 4), false, max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
-  a.use_lut = (o.variant & 4) ? 1 : 0;
+  a.use_lut = (o.variant & 4) ? 0 : 1;
+  a.compact = (o.variant & 32) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
@@ -1148,7 +1234,9 @@ extern "C" int gs_tune_3pcf(const gs_graph* G, const float* w, const gs_options*
   Opts o = read_opts(options);
   const int nconf = (int)num_conf3(g.nb);
   const int wmode = w ? kExact : kNone;
-  static const int kCandidates[4] = {0, 2, 4, 6};
+  // staged vs global hub rows, table vs computed configuration ranks, and
+  // (weighted) per-warp hit compaction
+  static const int kCandidates[6] = {0, 2, 4, 6, 32, 34};
   int best = 0;
   double best_ms = 1e300;
   int st = GS_OK;

@@ -7,7 +7,9 @@
 // byte) and looks each kept id up in N+(i) by binary search. The lookup
 // compares whole edge words, so it checks id and bin together. About one
 // word in nb reaches the lookup, so the kernel spends its time streaming the
-// spoke rows. Hub i's row is staged in shared memory when it fits. Counts
+// spoke rows, with 128-bit loads, and abandons a spoke row once its ids pass
+// the largest id of N+(i) (the merge-walk's exhaustion rule of Sec. 3.1).
+// Hub i's row is staged in shared memory when it fits. Counts
 // and weight sums build up in registers for each spoke and reach shared
 // memory once per spoke.
 #include <algorithm>
@@ -79,30 +81,42 @@ __global__ void __launch_bounds__(kEqThreads) k_equi3(const int64_t* __restrict_
     }
     const uint32_t* ri = staged ? srow : gi;
     const int64_t Wi = WEIGHTED ? W[i] : 0;
+    const uint32_t hub_hi = edge_id(ri[d - 1]);
     unsigned long long tri_warp = 0;
     for (int q = warp; q < d - 1; q += kEqWarps) {
       const uint32_t wj = ri[q];
       const uint32_t b = edge_bin(wj);
       const int64_t j = edge_id(wj);
       const uint32_t* rj = row_at(v.adj, ptr, j, v.off1, v.split, v.off2);
-      const int dj = deg[j];
+      const int dj4 = (int)pad_row(deg[j]);
       int cnt = 0;
       int64_t sw = 0;
-      for (int t = lane; t < dj; t += 32) {
-        const uint32_t wk = rj[t];
-        if (edge_bin(wk) != b) continue;
-        // N+(i) holds ids above j only after position q
-        int lo = q + 1, hi = d;
-        const uint32_t key = edge_id(wk);
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (edge_id(ri[mid]) < key) lo = mid + 1;
-          else hi = mid;
+      // N+(j) in 128-word chunks (four edge words per lane, padded rows),
+      // abandoned once its ids pass the largest id of N+(i)
+      for (int t0 = 0; t0 < dj4; t0 += 128) {
+        const int t = t0 + lane * 4;
+        const uint4 v4 = (t < dj4) ? ldg_nc_v4(rj + t)
+                                   : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+        const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const uint32_t wk = vv[qq];
+          const uint32_t key = edge_id(wk);
+          if (edge_bin(wk) != b || key > hub_hi) continue;
+          // N+(i) holds ids above j only after position q
+          int lo = q + 1, hi = d;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (edge_id(ri[mid]) < key) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo < d && ri[lo] == wk) {
+            ++cnt;
+            if (WEIGHTED) sw += W[key];
+          }
         }
-        if (lo < d && ri[lo] == wk) {
-          ++cnt;
-          if (WEIGHTED) sw += W[key];
-        }
+        const uint32_t last = __shfl_sync(0xffffffffu, v4.w, 31);
+        if (edge_id(last) > hub_hi) break;
       }
       for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);

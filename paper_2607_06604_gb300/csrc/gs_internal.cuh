@@ -152,6 +152,7 @@ struct FixedW {
   int64_t* d_W = nullptr;  // [n], internal order
   int scale = 0;
   int bits = 0;  // max bit length of |W_i| plus one sign bit
+  bool nonneg = true;  // no weight is negative
 };
 int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cudaStream_t s);
 
