@@ -70,7 +70,9 @@ typedef struct {
    * in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
    * global memory). 2 = gs_count_3pcf reads hub rows from global memory
    * instead of staging them. 4 = gs_count_3pcf computes configuration
-   * indices instead of looking them up in a shared table. 8 = gs_count_3pcf
+   * indices instead of looking them up in a shared table, and
+   * gs_count_4pcf* bins the non-hub edges by binary search over the bin
+   * edges instead of squared-distance buckets. 8 = gs_count_3pcf
    * limits its direct-address table to 2 KB (rows split at their largest id
    * gap, or hashed). 16 = gs_count_3pcf gives each block's first staging
    * wait no polls, so the call fails with GS_ETIMEOUT after the blocks have

@@ -32,6 +32,10 @@ namespace {
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSmemRow = 512;
+// Squared-distance buckets for the bin lookup: bucket k covers
+// [k 2^shift, (k + 1) 2^shift) with 2^shift no wider than the narrowest bin
+// in squared distance, so a bucket holds at most one bin edge.
+constexpr int kBucketMax = 2048;
 
 struct Args {
   const int64_t* __restrict__ ptr;
@@ -49,6 +53,7 @@ struct Args {
   int mcap;   // shared-memory workspace capacity (neighbours)
   int thr;    // hubs with more neighbours than this use the global workspace
   int gcap;   // global workspace capacity (neighbours)
+  int bk_shift, bk_n;  // squared-distance buckets (bk_n = 0: binary search)
   unsigned long long* even;
   unsigned long long* odd;
   unsigned long long* weven;  // [n_orbits][3] 192-bit
@@ -68,9 +73,15 @@ __device__ inline int64_t mi(int64_t d, int64_t box) {
   return d;
 }
 
-// Largest b with e2[b] <= D2 (the caller knows D2 is an edge).
+// Largest b with e2[b] <= D2 (the caller knows D2 is an edge): the bucket
+// of D2 gives the bin of the bucket's start, and one comparison with the
+// next edge finishes it; without buckets, a binary search.
 template <class T>
-__device__ inline int bin_of(T D2, const T* e2, int nb) {
+__device__ inline int bin_of(T D2, const T* e2, int nb, const uint8_t* bk, int shift) {
+  if (bk) {
+    const int b = bk[(uint64_t)D2 >> shift];
+    return b + (D2 >= e2[b + 1] ? 1 : 0);
+  }
   int lo = 0, hi = nb;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -139,7 +150,8 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
 // capacity) and counts go straight to the global histograms. Returns false
 // when the staging copy timed out.
 template <bool PARITY, bool WEIGHTED, bool SMALLR, bool GW, class E2T>
-__device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned* h_even,
+__device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uint8_t* bk,
+                     unsigned* h_even,
                      int* h_odd, int64_t i, int m, uint64_t* bar, uint32_t& phase, int* s_row) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = a.nb;
@@ -173,8 +185,10 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned*
   for (int k = tid; k < m; k += kThreads) {
     const uint32_t id = edge_id(row[k]);
     const int4 Q = a.xyzp[id];
+    // the fourth component carries the hub edge's bin, so one 128-bit load
+    // gives a vertex's displacement and b_i,vertex
     w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
-                          (int)mi((int64_t)Q.z - P.z, a.box), 0);
+                          (int)mi((int64_t)Q.z - P.z, a.box), (int)edge_bin(row[k]));
     uint32_t h = (id * kHashMul) >> shift;
     const unsigned long long ent = ((unsigned long long)id << 32) | (unsigned)k;
     while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
@@ -242,20 +256,19 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned*
         __syncwarp();
         if (active) {
           const int sb = (int)(e >> 16), sc = (int)(e & 0xFFFFu);
-          const uint32_t wb = row[sb], wcw = row[sc];
           const int4 db = w.disp[sb], dc = w.disp[sc];
-          const int b02 = (int)edge_bin(wb), b03 = (int)edge_bin(wcw);
-          const int b13 = bin_of(d2<SMALLR>(da, dc), e2, nb);
-          const int b23 = bin_of(d2<SMALLR>(db, dc), e2, nb);
+          const int b02 = db.w, b03 = dc.w;
+          const int b13 = bin_of(d2<SMALLR>(da, dc), e2, nb, bk, a.bk_shift);
+          const int b23 = bin_of(d2<SMALLR>(db, dc), e2, nb, bk, a.bk_shift);
           const uint32_t ent =
-              a.lut[(((size_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
+              a.lut[(((uint32_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
           const int orbit = (int)(ent & 0x3FFFFFFFu);
           if (GW) atomicAdd(a.even + orbit, 1ull);
           else atomicAdd(h_even + orbit, 1u);
           long long plo = 0, phi = 0;
           // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
           if (WEIGHTED) {
-            mul_i128(Wia, a.W[edge_id(wb)] * a.W[edge_id(wcw)], &plo, &phi);
+            mul_i128(Wia, a.W[edge_id(row[sb])] * a.W[edge_id(row[sc])], &plo, &phi);
             atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
           }
           if (PARITY && (ent >> 31)) {
@@ -301,7 +314,7 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, unsigned*
       while (xb) {  // warp-uniform: every lane walks the same bits
         const int sb = wb0 * 32 + __ffs(xb) - 1;
         xb &= xb - 1u;
-        const int b12 = bin_of(d2<SMALLR>(da, w.disp[sb]), e2, nb);
+        const int b12 = bin_of(d2<SMALLR>(da, w.disp[sb]), e2, nb, bk, a.bk_shift);
         const uint32_t* brb = w.bits + sb * W;
         for (int wc = sb >> 5; wc < W; ++wc) {
           uint32_t x = bra[wc] & brb[wc];
@@ -334,6 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   __shared__ int s_flush;
   __shared__ unsigned long long s_pending;
   __shared__ E2T e2[kMaxBins4 + 1];
+  __shared__ uint8_t s_bk[kBucketMax];
   __shared__ int s_row;
 
   const int tid = threadIdx.x;
@@ -351,6 +365,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     if (PARITY) h_odd[k] = 0;
   }
   for (int b = tid; b <= a.nb; b += kThreads) e2[b] = (E2T)a.e2g[b];
+  for (int k = tid; k < a.bk_n; k += kThreads) {
+    const int64_t x = (int64_t)k << a.bk_shift;
+    int b = 0;
+    while (b + 1 < a.nb && a.e2g[b + 1] <= x) ++b;
+    s_bk[k] = (uint8_t)b;
+  }
+  const uint8_t* bk = a.bk_n ? s_bk : nullptr;
   if (tid == 0) {
     mbar_init(&bar, 1);
     s_pending = 0;
@@ -416,10 +437,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     const int m = a.deg[i];
     bool ok;
     if (m > a.thr)
-      ok = hub4<PARITY, WEIGHTED, SMALLR, true>(a, ws_g, e2, h_even, h_odd, i, m, &bar, phase,
+      ok = hub4<PARITY, WEIGHTED, SMALLR, true>(a, ws_g, e2, bk, h_even, h_odd, i, m, &bar, phase,
                                                 &s_row);
     else
-      ok = hub4<PARITY, WEIGHTED, SMALLR, false>(a, ws_s, e2, h_even, h_odd, i, m, &bar, phase,
+      ok = hub4<PARITY, WEIGHTED, SMALLR, false>(a, ws_s, e2, bk, h_even, h_odd, i, m, &bar, phase,
                                                  &s_row);
     if (!ok) return;
   }
@@ -498,8 +519,10 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   const size_t hist_aligned = (hist_bytes + 15) & ~(size_t)15;
   // largest smem row that fits next to the histograms
   int mcap = kMaxSmemRow;
-  while (mcap > 32 && hist_aligned + workspace_bytes(mcap) > (size_t)optin - 1024) mcap -= 32;
-  if (hist_aligned + workspace_bytes(mcap) > (size_t)optin - 1024) return GS_ERANGE;
+  // static shared memory: the bucket table, the bin edges and a few words
+  const size_t avail = (size_t)optin - 1024 - kBucketMax;
+  while (mcap > 32 && hist_aligned + workspace_bytes(mcap) > avail) mcap -= 32;
+  if (hist_aligned + workspace_bytes(mcap) > avail) return GS_ERANGE;
 
   const bool small_r = g.edges[g.nb] < 32768;
   auto pick = [&]() -> void (*)(Args) {
@@ -526,6 +549,23 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   a.mcap = mcap;
   a.thr = thr;
   a.gcap = std::max(g.max_deg, 3);
+  // squared-distance buckets no wider than the narrowest bin (variant 4:
+  // binary search instead)
+  a.bk_shift = 0;
+  a.bk_n = 0;
+  if (!(o.variant & 4)) {
+    int64_t gap = INT64_MAX;
+    for (int b = 0; b < g.nb; ++b)
+      gap = std::min(gap, g.edges[b + 1] * g.edges[b + 1] - g.edges[b] * g.edges[b]);
+    int sh = 0;
+    while (sh < 62 && (int64_t(1) << (sh + 1)) <= gap) ++sh;
+    const int64_t top = g.edges[g.nb] * g.edges[g.nb];
+    const int64_t nbk = ((top - 1) >> sh) + 1;
+    if (gap >= 1 && nbk <= kBucketMax) {
+      a.bk_shift = sh;
+      a.bk_n = (int)nbk;
+    }
+  }
   a.gscratch = nullptr;
   a.gscratch_stride = 0;
   if (g.max_deg > thr) {

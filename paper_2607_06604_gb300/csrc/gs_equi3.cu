@@ -83,20 +83,48 @@ __global__ void __launch_bounds__(kEqThreads) k_equi3(const int64_t* __restrict_
     const int64_t Wi = WEIGHTED ? W[i] : 0;
     const uint32_t hub_hi = edge_id(ri[d - 1]);
     unsigned long long tri_warp = 0;
-    for (int q = warp; q < d - 1; q += kEqWarps) {
-      const uint32_t wj = ri[q];
+    const uint4 none = make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+    // The warp takes spokes q = warp, warp + kEqWarps, ...; the next spoke's
+    // row pointer, length and first chunk are loaded while the current one
+    // is walked, and so is the next chunk of the current row.
+    int q = warp;
+    uint32_t wj = 0;
+    const uint32_t* rj = nullptr;
+    int dj4 = 0;
+    uint4 v0 = none;
+    if (q < d - 1) {
+      wj = ri[q];
+      rj = row_at(v.adj, ptr, edge_id(wj), v.off1, v.split, v.off2);
+      dj4 = (int)pad_row(deg[edge_id(wj)]);
+      v0 = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
+    }
+    while (q < d - 1) {
+      const int qn = q + kEqWarps;
+      uint32_t wjn = 0;
+      const uint32_t* rjn = nullptr;
+      int dj4n = 0;
+      uint4 vn0 = none;
+      if (qn < d - 1) {
+        wjn = ri[qn];
+        rjn = row_at(v.adj, ptr, edge_id(wjn), v.off1, v.split, v.off2);
+        dj4n = (int)pad_row(deg[edge_id(wjn)]);
+        vn0 = (lane * 4 < dj4n) ? ldg_nc_v4(rjn + lane * 4) : none;
+      }
       const uint32_t b = edge_bin(wj);
       const int64_t j = edge_id(wj);
-      const uint32_t* rj = row_at(v.adj, ptr, j, v.off1, v.split, v.off2);
-      const int dj4 = (int)pad_row(deg[j]);
       int cnt = 0;
       int64_t sw = 0;
       // N+(j) in 128-word chunks (four edge words per lane, padded rows),
       // abandoned once its ids pass the largest id of N+(i)
-      for (int t0 = 0; t0 < dj4; t0 += 128) {
-        const int t = t0 + lane * 4;
-        const uint4 v4 = (t < dj4) ? ldg_nc_v4(rj + t)
-                                   : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
+      uint4 v4 = v0;
+      for (int t0 = 0;; t0 += 128) {
+        const uint32_t last = __shfl_sync(0xffffffffu, v4.w, 31);
+        const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
+        uint4 vnext = none;
+        if (more) {
+          const int t = t0 + 128 + lane * 4;
+          vnext = (t < dj4) ? ldg_nc_v4(rj + t) : none;
+        }
         const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
@@ -115,8 +143,8 @@ __global__ void __launch_bounds__(kEqThreads) k_equi3(const int64_t* __restrict_
             if (WEIGHTED) sw += W[key];
           }
         }
-        const uint32_t last = __shfl_sync(0xffffffffu, v4.w, 31);
-        if (edge_id(last) > hub_hi) break;
+        if (!more) break;
+        v4 = vnext;
       }
       for (int o = 16; o; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -131,6 +159,11 @@ __global__ void __launch_bounds__(kEqThreads) k_equi3(const int64_t* __restrict_
           atomic_add_i128(s_w + 2 * b, plo, phi);
         }
       }
+      q = qn;
+      wj = wjn;
+      rj = rjn;
+      dj4 = dj4n;
+      v0 = vn0;
     }
     if (WEIGHTED && lane == 0 && tri_warp) atomicAdd(&s_tri, tri_warp);
   }

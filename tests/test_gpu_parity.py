@@ -267,6 +267,11 @@ def test_4pcf_parity_clustered(gs, torch_mod, periodic, nb, seed):
     assert re.sum() > 100_000 and np.abs(ro).sum() > 0
     assert np.array_equal(ge, re)
     assert np.array_equal(go, ro)
+    # variant 4 bins the three non-hub edges by binary search over the edges
+    # instead of the squared-distance buckets
+    g = gs.gs_build_graph(dev(torch_mod, X), bu, edges)
+    be, bo = gs.gs_count_4pcf_parity(g, like=dev(torch_mod, np.zeros(1)), variant=4)
+    assert np.array_equal(be.cpu().numpy(), re) and np.array_equal(bo.cpu().numpy(), ro)
 
 
 def test_4pcf_weighted(gs, torch_mod):
