@@ -817,7 +817,7 @@ int gs_count_3pcf_equilateral(const gs_graph* G, const float* w, uint64_t* count
     uint64_t* dc = is_device_ptr(counts) ? counts : sc.alloc<uint64_t>(g.nb);
     double* dw = wsum ? (is_device_ptr(wsum) ? wsum : sc.alloc<double>(g.nb)) : nullptr;
     if (!dc || (wsum && !dw)) return GS_ENOMEM;
-    st = equi3_device(g, w ? &fw : nullptr, dc, dw, o, sc);
+    st = count3_device(g, w ? &fw : nullptr, dc, dw, o, sc, /*equi=*/true);
     OutBuf outs[2] = {{counts, dc, sizeof(uint64_t) * g.nb}, {wsum, dw, sizeof(double) * g.nb}};
     for (auto& b : outs)
       if (!st && b.user && b.dev != b.user)

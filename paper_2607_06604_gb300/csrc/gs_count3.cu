@@ -79,13 +79,19 @@ struct Smem {
   unsigned* hacc;      // 3 nconf: the current hub's 96-bit sums of W_j W_k (lo, mid, hi)
 };
 
+// LUT: the configuration table is staged (a launch-time choice, compiled in
+// so that the arithmetic rank is not carried along on the table path).
+template <bool LUT>
 __device__ inline int conf_index(const Smem& sm, int bij, int bik, int bjk, int nb) {
-  return sm.lut ? (int)sm.lut[(bij * nb + bik) * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
+  if constexpr (LUT) return (int)sm.lut[(bij * nb + bik) * nb + bjk];
+  else return conf3_rank(bij, bik, bjk, nb);
 }
 
 // The same with the table row of b_ij precomputed (lbase = b_ij nb^2).
+template <bool LUT>
 __device__ inline int conf_at(const Smem& sm, int lbase, int bij, int bik, int bjk, int nb) {
-  return sm.lut ? (int)sm.lut[lbase + bik * nb + bjk] : conf3_rank(bij, bik, bjk, nb);
+  if constexpr (LUT) return (int)sm.lut[lbase + bik * nb + bjk];
+  else return conf3_rank(bij, bik, bjk, nb);
 }
 
 // Weight modes: kNone and kExact (fixed-point integers: exact 128-bit
@@ -145,7 +151,10 @@ __device__ inline WType<WM> wget(const Cat& c, int64_t k) {
   else return 0;
 }
 
-template <int WM, bool SMEM_HIST, bool BATCH>
+// EQUI: equilateral configurations only (all three sides in one bin, the
+// configurations (b, b, b)): words of N+(j) in another bin than b_ij are not
+// probed, hits need b_ik = b_ij, and the histograms have nb entries.
+template <int WM, bool SMEM_HIST, bool BATCH, bool LUT, bool EQUI = false>
 __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
   constexpr bool WEIGHTED = WM != kNone;
   using WT = WType<WM>;
@@ -478,14 +487,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const uint32_t key = edge_id(vv[q]);
-              ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo);
+              ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo) &&
+                      (!EQUI || edge_bin(vv[q]) == (uint32_t)bij);
               off[q] = ok[q] ? slot(key) : 0u;
             }
           } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const uint32_t key = edge_id(vv[q]);
-              ok[q] = key <= hub_hi;
+              ok[q] = key <= hub_hi && (!EQUI || edge_bin(vv[q]) == (uint32_t)bij);
               off[q] = ok[q] ? key - base : 0u;
             }
           }
@@ -512,9 +522,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               for (int r = lane; r < n; r += 32) {
                 const uint32_t e = wq[r];
                 const WT packed = wst[e & 0xFFFFu];
-                record<WM, SMEM_HIST>(
-                    sm, c, conf_at(sm, lbase, bij, (int)(packed & 0xFF), (int)(e >> 16), nb), Wsp,
-                    packed >> 8);
+                if (!EQUI || (int)(packed & 0xFF) == bij)
+                  record<WM, SMEM_HIST>(
+                      sm, c,
+                      EQUI ? bij
+                           : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF), (int)(e >> 16), nb),
+                      Wsp, packed >> 8);
               }
               __syncwarp();
             } else {
@@ -524,10 +537,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
                 if (ok[q] && (bw[q].x & bit)) {
                   const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
                   const WT packed = wst[pos];
-                  record<WM, SMEM_HIST>(
-                      sm, c,
-                      conf_at(sm, lbase, bij, (int)(packed & 0xFF), (int)edge_bin(vv[q]), nb),
-                      Wsp, packed >> 8);
+                  if (!EQUI || (int)(packed & 0xFF) == bij)
+                    record<WM, SMEM_HIST>(
+                        sm, c,
+                        EQUI ? bij
+                             : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF),
+                                            (int)edge_bin(vv[q]), nb),
+                        Wsp, packed >> 8);
                 }
               }
             }
@@ -537,10 +553,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
             for (int q = 0; q < 4; ++q) bik[q] = sm.table[off[q]];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              if (ok[q] && bik[q] != kAbsent)
-                record<WM, SMEM_HIST>(sm, c,
-                                      conf_at(sm, lbase, bij, bik[q], (int)edge_bin(vv[q]), nb),
-                                      WT(0), WT(0));
+              if (ok[q] && bik[q] != kAbsent && (!EQUI || bik[q] == bij))
+                record<WM, SMEM_HIST>(
+                    sm, c, EQUI ? bij : conf_at<LUT>(sm, lbase, bij, bik[q], (int)edge_bin(vv[q]), nb),
+                    WT(0), WT(0));
           }
           if (more) {
             t0 += 128;
@@ -627,15 +643,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const uint32_t key = edge_id(vv[q]);
-            if (key > seg_hi) continue;
+            if (key > seg_hi || (EQUI && edge_bin(vv[q]) != (uint32_t)bij)) continue;
             uint32_t h = (key * kHashMul) >> shift;
             for (;;) {
               const uint32_t e = table[h];
               if (e == kSentinel) break;
               if (edge_id(e) == key) {
-                record<WM, SMEM_HIST>(
-                    sm, c, conf_index(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb), Wsp,
-                    wget<WM>(c, key));
+                if (!EQUI || (int)edge_bin(e) == bij)
+                  record<WM, SMEM_HIST>(
+                      sm, c,
+                      EQUI ? bij
+                           : conf_index<LUT>(sm, bij, (int)edge_bin(e), (int)edge_bin(vv[q]), nb),
+                      Wsp, wget<WM>(c, key));
                 break;
               }
               h = (h + 1) & (T - 1);
@@ -657,6 +676,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
 }
 
 
+// The instantiation of k_count3 for a launch: weight mode (nonnegative
+// weights take the cheaper carry chain), shared or global histograms,
+// single or batched, staged configuration table or arithmetic ranks.
+template <bool BATCH>
+void (*pick_count3(int wm, bool nonneg, bool smem_hist, bool lut))(Args) {
+#define GS_K(W, S) (lut ? k_count3<W, S, BATCH, true> : k_count3<W, S, BATCH, false>)
+  if (wm == kNone) return smem_hist ? GS_K(kNone, true) : GS_K(kNone, false);
+  if (!smem_hist) return GS_K(kExact, false);
+  return nonneg ? GS_K(kExactPos, true) : GS_K(kExact, true);
+#undef GS_K
+}
+
+void (*pick_equi3(int wm, bool nonneg, bool smem_hist))(Args) {
+  if (wm == kNone)
+    return smem_hist ? k_count3<kNone, true, false, false, true>
+                     : k_count3<kNone, false, false, false, true>;
+  if (!smem_hist) return k_count3<kExact, false, false, false, true>;
+  return nonneg ? k_count3<kExactPos, true, false, false, true>
+                : k_count3<kExact, true, false, false, true>;
+}
+
 // Shared-memory layout of k_count3: the direct-address table takes what the
 // staging buffer, configuration table and histograms leave.
 struct Count3Launch {
@@ -664,6 +704,7 @@ struct Count3Launch {
   int span_cap = 0;
   int stage_words = 0;
   bool smem_hist = true;
+  bool lut = false;  // the configuration table is staged
 };
 
 // Hubs with more than kMaxSmemHistDeg neighbours could overflow the 32-bit
@@ -684,6 +725,7 @@ Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, bool comp
   // counts, then (weighted) the CTA's 128-bit sums and the hub's 96-bit sums
   size_t hist = pad16((size_t)nconf * 4) + (wmode >= kExact ? pad16((size_t)nconf * 28) : 0);
   Count3Launch L;
+  L.lut = lut != 0;
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
   const size_t stage_words = weighted ? 2048 : kStageCap;
   const size_t queue = (weighted && compact) ? (size_t)kWarps * 128 * 4 : 0;
@@ -749,11 +791,12 @@ __global__ void k_u64_to_double(const unsigned long long* c, int64_t n, double* 
 int resolve_variant(const Graph& g, int wmode, int variant);
 
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
-                  const Opts& o_in, Scratch& sc) {
+                  const Opts& o_in, Scratch& sc, bool equi) {
   Opts o = o_in;
-  o.variant = resolve_variant(g, (fw && d_wsum) ? 2 : 0, o.variant);
+  o.variant = equi ? std::max(o.variant, 0) : resolve_variant(g, (fw && d_wsum) ? 2 : 0, o.variant);
   cudaStream_t s = o.stream;
-  const int nconf = (int)num_conf3(g.nb);
+  // the equilateral configurations (b, b, b) are indexed by b
+  const int nconf = equi ? g.nb : (int)num_conf3(g.nb);
   Args a;
   a.one.ptr = g.d_ptr;
   a.one.deg = g.d_deg;
@@ -786,21 +829,20 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
     return cuda_status(cudaGetLastError());
   }
 
+  const bool use_lut = !equi && !(o.variant & 4);
   const Count3Launch L =
-      count3_launch(g.nb, nconf, wm, !(o.variant & 4), (o.variant & 32) != 0, g.max_deg);
+      count3_launch(g.nb, nconf, wm, use_lut, (o.variant & 32) != 0, g.max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
-  a.use_lut = (o.variant & 4) ? 0 : 1;
+  a.use_lut = use_lut ? 1 : 0;
   a.compact = (o.variant & 32) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
-  if (wm == kExact)
-    kern = !smem_hist ? k_count3<kExact, false, false>
-           : fw->nonneg ? k_count3<kExactPos, true, false> : k_count3<kExact, true, false>;
-  else kern = smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
+  kern = equi ? pick_equi3(wm, fw && fw->nonneg, smem_hist)
+              : pick_count3<false>(wm, fw && fw->nonneg, smem_hist, L.lut);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -902,10 +944,7 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   void (*kern)(Args);
   bool nonneg = true;
   for (int k = 0; k < ng && fws; ++k) nonneg = nonneg && fws[k].nonneg;
-  if (wm == kExact)
-    kern = !smem_hist ? k_count3<kExact, false, true>
-           : nonneg ? k_count3<kExactPos, true, true> : k_count3<kExact, true, true>;
-  else kern = smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
+  kern = pick_count3<true>(wm, nonneg, smem_hist, L.lut);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -1046,7 +1085,7 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.compact = 0;
     a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
-    void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, false> : k_count3<kNone, false, false>;
+    void (*kern)(Args) = pick_count3<false>(kNone, true, L.smem_hist, L.lut);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -1145,7 +1184,7 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.compact = (o.variant & 32) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
-  void (*kern)(Args) = L.smem_hist ? k_count3<kNone, true, true> : k_count3<kNone, false, true>;
+  void (*kern)(Args) = pick_count3<true>(kNone, true, L.smem_hist, L.lut);
   int per_sm = 0, sms = 0, dev = 0;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
   cudaGetDevice(&dev);

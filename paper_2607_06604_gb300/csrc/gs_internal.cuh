@@ -159,8 +159,9 @@ int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cu
 // Kernel launchers (defined in the per-stage .cu files).
 int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
                        const std::vector<int64_t>& edges, const Opts& o, Graph* g);
+// equi: the equilateral configurations (b, b, b) only, nb outputs.
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
-                  const Opts& o, Scratch& sc);
+                  const Opts& o, Scratch& sc, bool equi = false);
 int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
                         double* const* d_wsum, const Opts& o, Scratch& sc);
 int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
@@ -170,8 +171,6 @@ int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint
 int connected_device(const Graph& gdr, const FixedW& fdr, const Graph& gr, const FixedW& fr,
                      double* d_xi, double* d_even, double* d_odd, double* d_disc, double* d_conn,
                      const Opts& o, Scratch& sc);
-int equi3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
-                 const Opts& o, Scratch& sc);
 int walk_words_device(Graph* g);
 int quantize_device(const double* d_pos, int64_t n, int64_t box_u, int periodic, int32_t* d_xyz,
                     cudaStream_t s, Scratch& sc);

@@ -148,6 +148,12 @@ def test_equilateral_matches_oracle_and_full_3pcf(gs, periodic):
     sel = diagonal(len(edges) - 1)
     assert np.array_equal(gc, fc[sel]) and np.array_equal(gw, fw[sel])
     assert np.array_equal(gs.gs_count_3pcf_equilateral(g), c)
+    # every launch path: hash of the hub row (1), hub rows from global memory
+    # (2), a 2 KB table (8), compacted weighted hits (32)
+    for v in (1, 2, 8, 32):
+        vc, vw = gs.gs_count_3pcf_equilateral(g, w, variant=v)
+        assert np.array_equal(vc, c), v
+        assert np.array_equal(vw, gw), v
     # out-of-core windows and hub shards
     g3 = gs.gs_build_graph(X, bu, edges, force_windows=3)
     c3, w3 = gs.gs_count_3pcf_equilateral(g3, w)
