@@ -77,8 +77,10 @@ typedef struct {
    * gap, or hashed). 16 = gs_count_3pcf gives each block's first staging
    * wait no polls, so the call fails with GS_ETIMEOUT after the blocks have
    * let their copies land (tests of the failure path). 32 = weighted
-   * gs_count_3pcf compacts each warp's hits before recording them. Other
-   * results are identical; the bits exist for testing and tuning. */
+   * gs_count_3pcf compacts each warp's hits before recording them. 64 =
+   * gs_count_3pcf streams spoke rows through a per-warp ring of
+   * asynchronous copies (deeper prefetch). Other results are identical;
+   * the bits exist for testing and tuning. */
   int32_t variant;
   /* cudaStream_t for all device work; NULL = legacy default stream. */
   void* stream;

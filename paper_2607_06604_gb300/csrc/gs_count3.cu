@@ -36,6 +36,7 @@ constexpr int kStageCap = 4096;   // hub-row words staged in shared memory
 constexpr int kSegCap = 2048;     // hash path: hub-row words per segment
 constexpr int kHashMax = 8192;    // hash path: slots, >= 4 x segment words
 constexpr int kLutMax = 16384;    // nb^3 entries of the configuration table
+constexpr int kRing = 4;          // prefetch ring: 128-word slots per warp
 constexpr uint8_t kAbsent = 0xFF;
 
 // One catalogue's arrays. A batched launch carries one per catalogue.
@@ -63,6 +64,7 @@ struct Args {
   int stage_alloc;        // words of the staging buffer
   int use_lut;            // 1: configuration index from the shared table
   int compact;            // 1: weighted hits compacted per warp before recording
+  int ring;               // 1: spoke rows prefetched through a per-warp cp.async ring
   uint32_t first_wait_limit;  // polls allowed for a block's first staging wait
   unsigned long long* hub_counter;
   int* err;
@@ -73,6 +75,8 @@ struct Smem {
   uint32_t* stage;     // stage_alloc words
   int64_t* wst;        // weighted: stage_alloc staged weights of N+(i) (8 bytes each)
   uint32_t* queue;     // weighted, compacting launches: 128 hits per warp (or nullptr)
+  uint32_t* ring;      // prefetching launches: kRing 128-word slots per warp (or nullptr)
+  int* ring_sp;        // the spoke of each slot
   uint16_t* lut;       // nb^3 configuration indices (or nullptr)
   unsigned* hist;      // nconf
   unsigned long long* whist;  // 2 nconf (lo, hi) words: the CTA's 128-bit sums
@@ -170,6 +174,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     if (WEIGHTED) p += (size_t)a.stage_alloc * 8;
     sm.queue = (WEIGHTED && a.compact) ? reinterpret_cast<uint32_t*>(p) : nullptr;
     if (WEIGHTED && a.compact) p += (size_t)kWarps * 128 * 4;
+    sm.ring = a.ring ? reinterpret_cast<uint32_t*>(p) : nullptr;
+    if (a.ring) p += (size_t)kWarps * kRing * 128 * 4;
+    sm.ring_sp = a.ring ? reinterpret_cast<int*>(p) : nullptr;
+    if (a.ring) p += (size_t)kWarps * kRing * 4;
     const int nb3 = a.nb * a.nb * a.nb;
     sm.lut = (a.use_lut && nb3 <= kLutMax) ? reinterpret_cast<uint16_t*>(p) : nullptr;
     if (a.use_lut && nb3 <= kLutMax) p += ((nb3 * 2 + 15) / 16) * 16;
@@ -437,6 +445,160 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
       // one is probed.
       const uint4 none = make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
       const bool split = far_lo <= hub_hi;  // two table ranges (block-uniform)
+      uint32_t* wq = sm.queue ? sm.queue + warp * 128 : nullptr;
+        // probes and hits of one 128-word chunk (four edge words per lane) of
+        // a spoke row whose hub edge has bin bij
+      auto process = [&](const uint4 v, const int bij, const int lbase, const WT Wsp) {
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+        // all four probes are issued before any hit is handled, so their
+        // shared-memory latencies overlap; keys past the hub row probe
+        // slot 0 and are discarded
+        bool ok[4];
+        uint32_t off[4];
+        if (split) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t key = edge_id(vv[q]);
+            ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo) &&
+                    (!EQUI || edge_bin(vv[q]) == (uint32_t)bij);
+            off[q] = ok[q] ? slot(key) : 0u;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t key = edge_id(vv[q]);
+            ok[q] = key <= hub_hi && (!EQUI || edge_bin(vv[q]) == (uint32_t)bij);
+            off[q] = ok[q] ? key - base : 0u;
+          }
+        }
+        if (WEIGHTED) {
+          uint2 bw[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bw[q] = bm[off[q] >> 5];
+          if (wq) {
+            // compact the chunk's hits into the warp's queue, then record
+            // them one per lane (full lanes instead of four divergent passes)
+            int n = 0;
+            const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t bit = 1u << (off[q] & 31);
+              const bool hit = ok[q] && (bw[q].x & bit);
+              const uint32_t m = __ballot_sync(0xffffffffu, hit);
+              if (hit)
+                wq[n + __popc(m & lt)] =
+                    (bw[q].y + (uint32_t)__popc(bw[q].x & (bit - 1u))) | (edge_bin(vv[q]) << 16);
+              n += __popc(m);
+            }
+            __syncwarp();
+            for (int r = lane; r < n; r += 32) {
+              const uint32_t e = wq[r];
+              const WT packed = wst[e & 0xFFFFu];
+              if (!EQUI || (int)(packed & 0xFF) == bij)
+                record<WM, SMEM_HIST>(
+                    sm, c,
+                    EQUI ? bij
+                         : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF), (int)(e >> 16), nb),
+                    Wsp, packed >> 8);
+            }
+            __syncwarp();
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint32_t bit = 1u << (off[q] & 31);
+              if (ok[q] && (bw[q].x & bit)) {
+                const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
+                const WT packed = wst[pos];
+                if (!EQUI || (int)(packed & 0xFF) == bij)
+                  record<WM, SMEM_HIST>(
+                      sm, c,
+                      EQUI ? bij
+                           : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF),
+                                          (int)edge_bin(vv[q]), nb),
+                      Wsp, packed >> 8);
+              }
+            }
+          }
+        } else {
+          uint8_t bik[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bik[q] = sm.table[off[q]];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (ok[q] && bik[q] != kAbsent && (!EQUI || bik[q] == bij))
+              record<WM, SMEM_HIST>(
+                  sm, c, EQUI ? bij : conf_at<LUT>(sm, lbase, bij, bik[q], (int)edge_bin(vv[q]), nb),
+                  WT(0), WT(0));
+        }
+      };
+      if (sm.ring) {
+        // Spoke rows through a per-warp ring of kRing 128-word slots filled by
+        // asynchronous copies (cp.async, 16 bytes per lane), so kRing - 1
+        // chunks are in flight while one is processed. The chunk stream runs
+        // through the warp's spokes in order; chunks already issued for a
+        // spoke that the walk has abandoned (its ids passed hub_hi) are
+        // skipped. Each lane copies and later reads its own 16 bytes of a
+        // slot; the slot's spoke index is written by lane 0.
+        uint32_t* ring = sm.ring + (size_t)warp * kRing * 128;
+        int* rsp = sm.ring_sp + warp * kRing;
+        int psp = d, pdj4 = 0, pt0 = 0, dead = -1;
+        const uint32_t* prj = nullptr;
+        auto next_spoke = [&]() {
+          int q = 0;
+          if (lane == 0) q = atomicAdd(&s_next, 1);
+          q = __shfl_sync(0xffffffffu, q, 0);
+          psp = q;
+          pt0 = 0;
+          if (q < d - 1) {
+            const uint32_t w = hr[q];
+            prj = row_at(c.adj, c.ptr, edge_id(w), c.adj_off, c.split, c.adj_off2);
+            pdj4 = (int)pad_row(c.deg[edge_id(w)]);
+          }
+        };
+        auto produce = [&](int st) {
+          while (psp < d - 1 && (pt0 >= pdj4 || psp == dead)) next_spoke();
+          uint32_t* dst = ring + st * 128 + lane * 4;
+          if (psp < d - 1) {
+            const int t = pt0 + lane * 4;
+            if (t < pdj4) cp_async16(dst, prj + t);
+            else *reinterpret_cast<uint4*>(dst) = none;
+            pt0 += 128;
+          }
+          if (lane == 0) rsp[st] = psp < d - 1 ? psp : -1;
+          cp_async_commit();
+        };
+        next_spoke();
+        for (int st = 0; st < kRing - 1; ++st) produce(st);
+        int csp = -1, bij = 0, lbase = 0;
+        WT Wsp = 0;
+        for (int it = 0;; ++it) {
+          produce((it + kRing - 1) % kRing);
+          cp_async_wait<kRing - 1>();
+          __syncwarp();
+          const int st = it % kRing;
+          const int sp = rsp[st];
+          if (sp < 0) break;
+          const uint4 v = *reinterpret_cast<const uint4*>(ring + st * 128 + lane * 4);
+          if (sp != dead) {
+            if (sp != csp) {
+              csp = sp;
+              const uint32_t wij = hr[sp];
+              bij = (int)edge_bin(wij);
+              lbase = bij * nb * nb;
+              if (WEIGHTED) {
+                const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
+                Wsp = SMEM_HIST ? Wj : Wi * Wj;
+              }
+            }
+            process(v, bij, lbase, Wsp);
+            const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+            if (edge_id(last) > hub_hi) dead = sp;
+          }
+          __syncwarp();
+        }
+        cp_async_wait_all();
+        __syncwarp();
+      } else {
       int sp = 0;
       if (lane == 0) sp = atomicAdd(&s_next, 1);
       sp = __shfl_sync(0xffffffffu, sp, 0);
@@ -455,7 +617,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
           const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
           Wsp = SMEM_HIST ? Wj : Wi * Wj;
         }
-        uint32_t* wq = sm.queue ? sm.queue + warp * 128 : nullptr;
         for (;;) {
           const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
           const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
@@ -477,87 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               vn = (lane * 4 < ndj4) ? ldg_nc_v4(nrj + lane * 4) : none;
             }
           }
-          const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-          // all four probes are issued before any hit is handled, so their
-          // shared-memory latencies overlap; keys past the hub row probe
-          // slot 0 and are discarded
-          bool ok[4];
-          uint32_t off[4];
-          if (split) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t key = edge_id(vv[q]);
-              ok[q] = key <= hub_hi && (key <= near_hi || key >= far_lo) &&
-                      (!EQUI || edge_bin(vv[q]) == (uint32_t)bij);
-              off[q] = ok[q] ? slot(key) : 0u;
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint32_t key = edge_id(vv[q]);
-              ok[q] = key <= hub_hi && (!EQUI || edge_bin(vv[q]) == (uint32_t)bij);
-              off[q] = ok[q] ? key - base : 0u;
-            }
-          }
-          if (WEIGHTED) {
-            uint2 bw[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) bw[q] = bm[off[q] >> 5];
-            if (wq) {
-              // compact the chunk's hits into the warp's queue, then record
-              // them one per lane (full lanes instead of four divergent passes)
-              int n = 0;
-              const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const uint32_t bit = 1u << (off[q] & 31);
-                const bool hit = ok[q] && (bw[q].x & bit);
-                const uint32_t m = __ballot_sync(0xffffffffu, hit);
-                if (hit)
-                  wq[n + __popc(m & lt)] =
-                      (bw[q].y + (uint32_t)__popc(bw[q].x & (bit - 1u))) | (edge_bin(vv[q]) << 16);
-                n += __popc(m);
-              }
-              __syncwarp();
-              for (int r = lane; r < n; r += 32) {
-                const uint32_t e = wq[r];
-                const WT packed = wst[e & 0xFFFFu];
-                if (!EQUI || (int)(packed & 0xFF) == bij)
-                  record<WM, SMEM_HIST>(
-                      sm, c,
-                      EQUI ? bij
-                           : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF), (int)(e >> 16), nb),
-                      Wsp, packed >> 8);
-              }
-              __syncwarp();
-            } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const uint32_t bit = 1u << (off[q] & 31);
-                if (ok[q] && (bw[q].x & bit)) {
-                  const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
-                  const WT packed = wst[pos];
-                  if (!EQUI || (int)(packed & 0xFF) == bij)
-                    record<WM, SMEM_HIST>(
-                        sm, c,
-                        EQUI ? bij
-                             : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF),
-                                            (int)edge_bin(vv[q]), nb),
-                        Wsp, packed >> 8);
-                }
-              }
-            }
-          } else {
-            uint8_t bik[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) bik[q] = sm.table[off[q]];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (ok[q] && bik[q] != kAbsent && (!EQUI || bik[q] == bij))
-                record<WM, SMEM_HIST>(
-                    sm, c, EQUI ? bij : conf_at<LUT>(sm, lbase, bij, bik[q], (int)edge_bin(vv[q]), nb),
-                    WT(0), WT(0));
-          }
+          process(v, bij, lbase, Wsp);
           if (more) {
             t0 += 128;
           } else {
@@ -576,6 +657,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
           }
           v = vn;
         }
+      }
       }
       __syncthreads();
       fold_hub(Wi);
@@ -713,7 +795,7 @@ struct Count3Launch {
 constexpr int kMaxSmemHistDeg = 65535;
 
 Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, bool compact,
-                           int max_deg) {
+                           bool ring, int max_deg) {
   const bool weighted = wmode != kNone;
   // weighted launches stage rows and weights of up to 2048 neighbours
   int dev = 0, optin = 0;
@@ -729,7 +811,8 @@ Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, bool comp
   const size_t avail = (size_t)optin - 2048;  // static shared memory and slack
   const size_t stage_words = weighted ? 2048 : kStageCap;
   const size_t queue = (weighted && compact) ? (size_t)kWarps * 128 * 4 : 0;
-  const size_t fixed = stage_words * (weighted ? 12 : 4) + queue + lut;
+  const size_t ringb = ring ? (size_t)kWarps * kRing * (128 * 4 + 4) : 0;
+  const size_t fixed = stage_words * (weighted ? 12 : 4) + queue + ringb + lut;
   L.smem_hist = fixed + hist + 32 * 1024 <= avail && max_deg <= kMaxSmemHistDeg;
   if (!L.smem_hist) hist = 0;
   L.span_cap = (int)((avail - fixed - hist) & ~(size_t)15);
@@ -831,11 +914,13 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
 
   const bool use_lut = !equi && !(o.variant & 4);
   const Count3Launch L =
-      count3_launch(g.nb, nconf, wm, use_lut, (o.variant & 32) != 0, g.max_deg);
+      count3_launch(g.nb, nconf, wm, use_lut, (o.variant & 32) != 0, (o.variant & 64) != 0,
+                    g.max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = use_lut ? 1 : 0;
   a.compact = (o.variant & 32) ? 1 : 0;
+  a.ring = (o.variant & 64) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
@@ -932,11 +1017,13 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   int max_deg = 0;
   for (int k = 0; k < ng; ++k) max_deg = std::max(max_deg, gr[k]->max_deg);
   const Count3Launch L =
-      count3_launch(nb, nconf, wm, !(o.variant & 4), (o.variant & 32) != 0, max_deg);
+      count3_launch(nb, nconf, wm, !(o.variant & 4), (o.variant & 32) != 0, (o.variant & 64) != 0,
+                    max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 0 : 1;
   a.compact = (o.variant & 32) ? 1 : 0;
+  a.ring = (o.variant & 64) ? 1 : 0;
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   const bool smem_hist = L.smem_hist;
@@ -1078,11 +1165,13 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
     a.hub_counter = counter;
     a.err = err;
-    const Count3Launch L = count3_launch(g.nb, nconf, kNone, !(o.variant & 4), false, g.max_deg);
+    const Count3Launch L =
+        count3_launch(g.nb, nconf, kNone, !(o.variant & 4), false, false, g.max_deg);
     a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
     a.stage_alloc = L.stage_words;
     a.use_lut = (o.variant & 4) ? 0 : 1;
     a.compact = 0;
+    a.ring = 0;
     a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
     a.stage_cap = std::min(a.stage_cap, L.stage_words);
     void (*kern)(Args) = pick_count3<false>(kNone, true, L.smem_hist, L.lut);
@@ -1177,11 +1266,12 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
   a.err = P->err;
   int max_deg = 0;
   for (int k = 0; k < n_graphs; ++k) max_deg = std::max(max_deg, graphs[k]->g.max_deg);
-  const Count3Launch L = count3_launch(nb, nconf, kNone, !(o.variant & 4), false, max_deg);
+  const Count3Launch L = count3_launch(nb, nconf, kNone, !(o.variant & 4), false, false, max_deg);
   a.span_cap = (o.variant & 8) ? 2048 : L.span_cap;
   a.stage_alloc = L.stage_words;
   a.use_lut = (o.variant & 4) ? 0 : 1;
   a.compact = (o.variant & 32) ? 1 : 0;
+  a.ring = 0;  // recorded plans keep the default walk
   a.first_wait_limit = (o.variant & 16) ? 0u : kWaitLimit;
   a.stage_cap = std::min(a.stage_cap, L.stage_words);
   void (*kern)(Args) = pick_count3<true>(kNone, true, L.smem_hist, L.lut);
@@ -1273,9 +1363,9 @@ extern "C" int gs_tune_3pcf(const gs_graph* G, const float* w, const gs_options*
   Opts o = read_opts(options);
   const int nconf = (int)num_conf3(g.nb);
   const int wmode = w ? kExact : kNone;
-  // staged vs global hub rows, table vs computed configuration ranks, and
-  // (weighted) per-warp hit compaction
-  static const int kCandidates[6] = {0, 2, 4, 6, 32, 34};
+  // staged vs global hub rows, table vs computed configuration ranks,
+  // (weighted) per-warp hit compaction, and the spoke-row prefetch ring
+  static const int kCandidates[8] = {0, 2, 4, 6, 32, 34, 64, 96};
   int best = 0;
   double best_ms = 1e300;
   int st = GS_OK;

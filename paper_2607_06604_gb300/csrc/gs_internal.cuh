@@ -364,6 +364,21 @@ __device__ inline void bulk_load(void* smem_dst, const void* gmem_src, uint32_t 
       : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only). The
+// source and destination must be 16-byte aligned. Groups are per thread:
+// commit closes the thread's current group, wait<N> returns when at most N
+// of the thread's groups are still in flight.
+__device__ inline void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ inline uint4 ldg_nc_v4(const uint32_t* p) {
   uint4 v;
   asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"

@@ -176,7 +176,7 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     ex_c, ex_w = gs.gs_count_3pcf(g, w)
     assert np.array_equal(ex_c, rc)
     np.testing.assert_allclose(ex_w, rw, rtol=RTOL)
-    for variant in (1, 2, 4, 6, 8, 10, 32, 34, 36, 40):
+    for variant in (1, 2, 4, 6, 8, 10, 32, 34, 36, 40, 64, 68, 72, 96):
         vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(vc, rc), variant
         np.testing.assert_allclose(vw, gw, rtol=1e-13)

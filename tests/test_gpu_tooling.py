@@ -149,8 +149,8 @@ def test_equilateral_matches_oracle_and_full_3pcf(gs, periodic):
     assert np.array_equal(gc, fc[sel]) and np.array_equal(gw, fw[sel])
     assert np.array_equal(gs.gs_count_3pcf_equilateral(g), c)
     # every launch path: hash of the hub row (1), hub rows from global memory
-    # (2), a 2 KB table (8), compacted weighted hits (32)
-    for v in (1, 2, 8, 32):
+    # (2), a 2 KB table (8), compacted weighted hits (32), prefetch ring (64)
+    for v in (1, 2, 8, 32, 64, 72):
         vc, vw = gs.gs_count_3pcf_equilateral(g, w, variant=v)
         assert np.array_equal(vc, c), v
         assert np.array_equal(vw, gw), v
