@@ -456,8 +456,9 @@ def test_full_size_ddd_bit_exact(gs, torch_mod, ns1m):
 
 def test_full_size_rrr_properties(gs, torch_mod):
     """3e6 uniform randoms, L=1000, rmax 40 in 20 bins (too large for the
-    oracle): mirror and relabelling invariance hold bit for bit, and the
-    triangle total matches the Poisson closed form C(N,3) p^2 15/32."""
+    oracle): mirror and relabelling invariance hold bit for bit, the
+    triangle total matches the Poisson closed form C(N,3) p^2 15/32, and the
+    exact weighted sums obey the same invariances and exact scalings."""
     s = catalogs.draw("ns1M_L1000_r40_nb20")
     N = s["randoms"]
     pos = catalogs.uniform(N, s["box"], seed=s["random_seed"])
@@ -473,6 +474,19 @@ def test_full_size_rrr_properties(gs, torch_mod):
     expect = math.comb(N, 3) * p * p * 15 / 32
     sd = math.sqrt(expect) * 30  # generous: triangle counts are strongly correlated
     assert abs(float(c0.sum()) - expect) < 5 * sd
+    # the launch configuration the bench times: counts with exact weighted sums.
+    # Exact sums are invariant bit for bit under the mirror and a relabelling,
+    # equal the counts for unit weights and scale by exactly 8 when every
+    # weight doubles (2w is exact in FP32).
+    w = catalogs.uniform_weights(N, seed=s["weight_seed"] + 7)
+    cw, ws = run3(gs, torch_mod, X, box_u, s["edges_u"], w)
+    assert np.array_equal(cw, c0)
+    assert np.array_equal(run3(gs, torch_mod, Xm, box_u, s["edges_u"], w)[1], ws)
+    assert np.array_equal(run3(gs, torch_mod, X[perm], box_u, s["edges_u"], w[perm])[1], ws)
+    ones = np.ones(N, dtype=np.float32)
+    assert np.array_equal(run3(gs, torch_mod, X, box_u, s["edges_u"], ones)[1],
+                          c0.astype(np.float64))
+    assert np.array_equal(run3(gs, torch_mod, X, box_u, s["edges_u"], 2 * w)[1], 8 * ws)
 
 
 def test_4pcf_parity_clustered_workload_density(gs, torch_mod):
