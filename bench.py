@@ -80,7 +80,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_VERSION = "k_count3.v12"  # bump when k_count3 changes; stale captures then report null
+KERNEL_VERSION = "k_count3.v13"  # bump when k_count3 changes; stale captures then report null
 
 
 def recorded_traffic():

@@ -73,7 +73,7 @@ struct Args {
 struct Smem {
   uint8_t* table;      // span_cap bytes; the hash path reuses it as words
   uint32_t* stage;     // stage_alloc words
-  int64_t* wst;        // weighted: stage_alloc staged weights of N+(i) (8 bytes each)
+  int64_t* wst;        // weighted: stage_alloc (W_k, bin(i, k)) pairs of N+(i), 8 bytes each
   uint32_t* queue;     // weighted, compacting launches: 128 hits per warp (or nullptr)
   uint32_t* ring;      // prefetching launches: kRing 128-word slots per warp (or nullptr)
   int* ring_sp;        // the spoke of each slot
@@ -129,10 +129,8 @@ __device__ inline void record(const Smem& sm, const Cat& c, int cf, WType<WM> Ws
       if constexpr (WM == kExactPos) {
         // 0 <= x < 2^60: x1 + c0 cannot wrap and the top limb only takes
         // the mid limb's carries
-        if (a1) {
-          const uint32_t o1 = atomicAdd(sm.hacc + 3 * cf + 1, a1);
-          if (o1 + a1 < o1) atomicAdd(sm.hacc + 3 * cf + 2, 1u);
-        }
+        const uint32_t o1 = atomicAdd(sm.hacc + 3 * cf + 1, a1);
+        if (o1 + a1 < o1) atomicAdd(sm.hacc + 3 * cf + 2, 1u);
       } else {
         uint32_t a2 = (x < 0 ? 0xFFFFFFFFu : 0u) + ((a1 < x1) ? 1u : 0u);
         if (a1) {
@@ -333,7 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
     }
     const uint32_t* row = row_at(c.adj, c.ptr, i, c.adj_off, c.split, c.adj_off2);
     const WT Wi = wget<WM>(c, i);
-    WT* wst = reinterpret_cast<WT*>(sm.wst);
+    // staged (W_k, bin(i, k)) pairs: one 64-bit load per hit, |W_k| < 2^30
+    int2* wst2 = reinterpret_cast<int2*>(sm.wst);
     const uint32_t hub_hi = edge_id(row[d - 1]);
     const int64_t span = (int64_t)hub_hi - i;  // ids i+1 .. hub_hi
     const bool staged = d <= a.stage_cap;
@@ -355,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         if (WEIGHTED)
           for (int k = tid; k < d; k += kThreads) {
             const uint32_t w = row[k];
-            wst[k] = wget<WM>(c, edge_id(w)) * 256 + (WT)edge_bin(w);
+            wst2[k] = make_int2((int)wget<WM>(c, edge_id(w)), (int)edge_bin(w));
           }
         if (!wait_stage()) return;
         hr = sm.stage;
@@ -493,13 +492,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
             __syncwarp();
             for (int r = lane; r < n; r += 32) {
               const uint32_t e = wq[r];
-              const WT packed = wst[e & 0xFFFFu];
-              if (!EQUI || (int)(packed & 0xFF) == bij)
+              const int2 pk = wst2[e & 0xFFFFu];
+              if (!EQUI || pk.y == bij)
                 record<WM, SMEM_HIST>(
-                    sm, c,
-                    EQUI ? bij
-                         : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF), (int)(e >> 16), nb),
-                    Wsp, packed >> 8);
+                    sm, c, EQUI ? bij : conf_at<LUT>(sm, lbase, bij, pk.y, (int)(e >> 16), nb), Wsp,
+                    (WT)pk.x);
             }
             __syncwarp();
           } else {
@@ -508,14 +505,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               const uint32_t bit = 1u << (off[q] & 31);
               if (ok[q] && (bw[q].x & bit)) {
                 const int pos = (int)bw[q].y + __popc(bw[q].x & (bit - 1u));
-                const WT packed = wst[pos];
-                if (!EQUI || (int)(packed & 0xFF) == bij)
+                const int2 pk = wst2[pos];
+                if (!EQUI || pk.y == bij)
                   record<WM, SMEM_HIST>(
                       sm, c,
-                      EQUI ? bij
-                           : conf_at<LUT>(sm, lbase, bij, (int)(packed & 0xFF),
-                                          (int)edge_bin(vv[q]), nb),
-                      Wsp, packed >> 8);
+                      EQUI ? bij : conf_at<LUT>(sm, lbase, bij, pk.y, (int)edge_bin(vv[q]), nb),
+                      Wsp, (WT)pk.x);
               }
             }
           }
@@ -586,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
               bij = (int)edge_bin(wij);
               lbase = bij * nb * nb;
               if (WEIGHTED) {
-                const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
+                const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
                 Wsp = SMEM_HIST ? Wj : Wi * Wj;
               }
             }
@@ -614,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         int lbase = bij * nb * nb;
         WT Wsp = 0;
         if (WEIGHTED) {
-          const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
+          const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
           Wsp = SMEM_HIST ? Wj : Wi * Wj;
         }
         for (;;) {
@@ -651,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
             bij = (int)edge_bin(wij);
             lbase = bij * nb * nb;
             if (WEIGHTED) {
-              const WT Wj = staged ? (wst[sp] >> 8) : wget<WM>(c, edge_id(wij));
+              const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
               Wsp = SMEM_HIST ? Wj : Wi * Wj;
             }
           }
