@@ -343,8 +343,8 @@ def run_ours(args):
     traffic = recorded_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-            "limiter": "instruction issue (ncu: 79% of issue slots busy, integer ALU pipe 66%, "
-                       "L1/shared pipe 65%, L2 hit 98.9%, DRAM 0.09%): spoke rows are re-read "
+            "limiter": "instruction issue (ncu: 77% of issue slots busy, integer ALU pipe 59%, "
+                       "L1/shared pipe 71%, L2 hit 98.9%, DRAM 0.09%): spoke rows are re-read "
                        "from L2",
             "kernel": "k_count3 (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
             "triangles_per_launch": float(counts[1].sum().item())}
