@@ -490,7 +490,6 @@ def make_mocks(count, nmax, seed=11):
     3pCF rmax 60 in 12 bins; the first 32 also ask for the 4pCF (rmax 25,
     6 bins). A 128^3 field keeps host generation to a fraction of a second
     per catalogue."""
-    import oracle  # noqa: F401  (not used: quantisation below is the library's)
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = np.exp(rng.uniform(np.log(5e4), np.log(nmax), size=count)).astype(int)
     L = 500.0
