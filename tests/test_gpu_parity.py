@@ -184,6 +184,29 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
         assert np.array_equal(gs.gs_count_3pcf(g, w, variant=variant)[1], ex_w)
 
 
+def test_3pcf_signed_weights(gs, torch_mod):
+    """Weights of both signs take the general carry chain of the exact sums
+    (nonnegative weights take a cheaper one): every launch path agrees with
+    the oracle's exact sums, and negating every weight negates the sums."""
+    L = 150.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(30_000, L, seed=15, sigma=2.0, periodic=True)
+    X = oracle.quantize(pos, box_u, True)
+    w = catalogs.uniform_weights(len(X), seed=16)
+    sign = np.where(np.random.default_rng(17).random(len(X)) < 0.5, -1.0, 1.0)
+    w = (w * sign).astype(np.float32)
+    edges = catalogs.bin_edges_u(0.0, 12.0, 8)
+    rc, rw = oracle.Graph(X, box_u, edges).count_3pcf(w)
+    assert np.any(rw < 0) and np.any(rw > 0)
+    g = gs.gs_build_graph(X, box_u, edges)
+    for variant in (0, 1, 4, 32, 64):
+        gc, gw = gs.gs_count_3pcf(g, w, variant=variant)
+        assert np.array_equal(gc, rc), variant
+        np.testing.assert_allclose(gw, rw, rtol=RTOL, atol=0, err_msg=str(variant))
+    _, gn = gs.gs_count_3pcf(g, -w)
+    assert np.array_equal(gn, -gs.gs_count_3pcf(g, w)[1])
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
 def test_3pcf_tiny_and_empty(gs, torch_mod, n):
     box_u = 100_000
