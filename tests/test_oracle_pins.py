@@ -135,6 +135,22 @@ def test_3pcf_weighted_exact():
     assert np.array_equal(w2, 8 * ws)
 
 
+def test_3pcf_signed_weights_exact():
+    """Weights of both signs (the signed estimator's case): the oracle's exact
+    sums against exact rational sums over all triples."""
+    box_u = 30_000
+    edges_u = np.array([0, 2500, 5000, 7000], dtype=np.int64)
+    X = clustered_lattice(100, box_u, 7, 4000)
+    w = catalogs.uniform_weights(X.shape[0], seed=9)
+    sign = np.where(np.random.default_rng(10).random(len(w)) < 0.5, -1.0, 1.0)
+    w = (w * sign).astype(np.float32)
+    ref_c, ref_w = bf.count3(X, box_u, edges_u, w)
+    assert np.any(ref_w < 0) and np.any(ref_w > 0)
+    c, ws = oracle.Graph(X, box_u, edges_u, nthreads=2).count_3pcf(w)
+    assert np.array_equal(c, ref_c)
+    np.testing.assert_allclose(ws, ref_w, rtol=1e-15, atol=0)
+
+
 def test_3pcf_poisson_closed_form():
     """Unbinned triangle total of a uniform periodic catalogue.
 
