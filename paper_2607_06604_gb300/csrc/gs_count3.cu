@@ -439,14 +439,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         }
       }
       __syncthreads();
-      // Each warp walks spoke rows in 128-word chunks; the next chunk, or the
-      // first chunk of the warp's next spoke, is loaded before the current
-      // one is probed.
+      // Each warp walks spoke rows in 128-word chunks. By default the next
+      // chunk, or the first chunk of the warp's next spoke, is loaded into
+      // registers before the current one is probed.
       const uint4 none = make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
       const bool split = far_lo <= hub_hi;  // two table ranges (block-uniform)
       uint32_t* wq = sm.queue ? sm.queue + warp * 128 : nullptr;
-        // probes and hits of one 128-word chunk (four edge words per lane) of
-        // a spoke row whose hub edge has bin bij
+      // probes and hits of one 128-word chunk (four edge words per lane) of
+      // a spoke row whose hub edge has bin bij
       auto process = [&](const uint4 v, const int bij, const int lbase, const WT Wsp) {
         const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
         // all four probes are issued before any hit is handled, so their
@@ -594,65 +594,65 @@ __global__ void __launch_bounds__(kThreads, 1) k_count3(Args a) {
         cp_async_wait_all();
         __syncwarp();
       } else {
-      int sp = 0;
-      if (lane == 0) sp = atomicAdd(&s_next, 1);
-      sp = __shfl_sync(0xffffffffu, sp, 0);
-      if (sp < d - 1) {  // the last neighbour has no k above it
-        uint32_t wij = hr[sp];
-        const uint32_t* rj = row_at(c.adj, c.ptr, edge_id(wij), c.adj_off, c.split, c.adj_off2);
-        int dj4 = (int)pad_row(c.deg[edge_id(wij)]);
-        int t0 = 0;
-        uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
-        // per-spoke constants: b_ij, the spoke's weight factor, and the row of
-        // the configuration table that b_ij selects
-        int bij = (int)edge_bin(wij);
-        int lbase = bij * nb * nb;
-        WT Wsp = 0;
-        if (WEIGHTED) {
-          const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
-          Wsp = SMEM_HIST ? Wj : Wi * Wj;
-        }
-        for (;;) {
-          const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
-          const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
-          uint4 vn = none;
-          int nsp = sp;
-          uint32_t nwij = wij;
-          const uint32_t* nrj = rj;
-          int ndj4 = dj4;
-          if (more) {
-            const int t = t0 + 128 + lane * 4;
-            vn = (t < dj4) ? ldg_nc_v4(rj + t) : none;
-          } else {
-            if (lane == 0) nsp = atomicAdd(&s_next, 1);
-            nsp = __shfl_sync(0xffffffffu, nsp, 0);
-            if (nsp < d - 1) {
-              nwij = hr[nsp];
-              nrj = row_at(c.adj, c.ptr, edge_id(nwij), c.adj_off, c.split, c.adj_off2);
-              ndj4 = (int)pad_row(c.deg[edge_id(nwij)]);
-              vn = (lane * 4 < ndj4) ? ldg_nc_v4(nrj + lane * 4) : none;
-            }
+        int sp = 0;
+        if (lane == 0) sp = atomicAdd(&s_next, 1);
+        sp = __shfl_sync(0xffffffffu, sp, 0);
+        if (sp < d - 1) {  // the last neighbour has no k above it
+          uint32_t wij = hr[sp];
+          const uint32_t* rj = row_at(c.adj, c.ptr, edge_id(wij), c.adj_off, c.split, c.adj_off2);
+          int dj4 = (int)pad_row(c.deg[edge_id(wij)]);
+          int t0 = 0;
+          uint4 v = (lane * 4 < dj4) ? ldg_nc_v4(rj + lane * 4) : none;
+          // per-spoke constants: b_ij, the spoke's weight factor, and the row of
+          // the configuration table that b_ij selects
+          int bij = (int)edge_bin(wij);
+          int lbase = bij * nb * nb;
+          WT Wsp = 0;
+          if (WEIGHTED) {
+            const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
+            Wsp = SMEM_HIST ? Wj : Wi * Wj;
           }
-          process(v, bij, lbase, Wsp);
-          if (more) {
-            t0 += 128;
-          } else {
-            if (nsp >= d - 1) break;
-            sp = nsp;
-            wij = nwij;
-            rj = nrj;
-            dj4 = ndj4;
-            t0 = 0;
-            bij = (int)edge_bin(wij);
-            lbase = bij * nb * nb;
-            if (WEIGHTED) {
-              const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
-              Wsp = SMEM_HIST ? Wj : Wi * Wj;
+          for (;;) {
+            const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
+            const bool more = edge_id(last) <= hub_hi && t0 + 128 < dj4;
+            uint4 vn = none;
+            int nsp = sp;
+            uint32_t nwij = wij;
+            const uint32_t* nrj = rj;
+            int ndj4 = dj4;
+            if (more) {
+              const int t = t0 + 128 + lane * 4;
+              vn = (t < dj4) ? ldg_nc_v4(rj + t) : none;
+            } else {
+              if (lane == 0) nsp = atomicAdd(&s_next, 1);
+              nsp = __shfl_sync(0xffffffffu, nsp, 0);
+              if (nsp < d - 1) {
+                nwij = hr[nsp];
+                nrj = row_at(c.adj, c.ptr, edge_id(nwij), c.adj_off, c.split, c.adj_off2);
+                ndj4 = (int)pad_row(c.deg[edge_id(nwij)]);
+                vn = (lane * 4 < ndj4) ? ldg_nc_v4(nrj + lane * 4) : none;
+              }
             }
+            process(v, bij, lbase, Wsp);
+            if (more) {
+              t0 += 128;
+            } else {
+              if (nsp >= d - 1) break;
+              sp = nsp;
+              wij = nwij;
+              rj = nrj;
+              dj4 = ndj4;
+              t0 = 0;
+              bij = (int)edge_bin(wij);
+              lbase = bij * nb * nb;
+              if (WEIGHTED) {
+                const WT Wj = staged ? (WT)wst2[sp].x : wget<WM>(c, edge_id(wij));
+                Wsp = SMEM_HIST ? Wj : Wi * Wj;
+              }
+            }
+            v = vn;
           }
-          v = vn;
         }
-      }
       }
       __syncthreads();
       fold_hub(Wi);
