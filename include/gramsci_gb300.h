@@ -189,13 +189,14 @@ int gs_tune_3pcf(const gs_graph* g, const float* w, const gs_options* options,
  * gs_count_3pcf_noalloc - unweighted gs_count_3pcf that allocates nothing.
  * The paper has no counterpart: this entry point is for callers that may
  * not let a library allocate memory during a call (a process that gave all
- * device memory to its own pool, a real-time loop that must avoid the
- * allocator's locks and synchronisation, code that records its work for
- * replay and must keep the memory map fixed). Instead of allocating, it
+ * device memory to its own pool, so that any further allocation fails; a
+ * real-time loop that must avoid the allocator's locks and the device
+ * synchronisation that cudaFree implies). Instead of allocating, it
  * uses one fixed 64 KB scratch array compiled into the library, which every
  * GPU that loads the library holds until the process exits.
  *   g       a resident graph (not out-of-core), nb <= 35.
- *   counts  uint64 [C(nb+2,3)], host or device; identical to gs_count_3pcf.
+ *   counts  uint64 [C(nb+2,3)], host or device; identical to gs_count_3pcf
+ *           for every options->variant (-1 = the tuned variant).
  * The first call on each device looks up the scratch array's device address
  * (with that device current); make that first call before any stream
  * capture. All calls share the array and it keeps the last call's contents:

@@ -28,6 +28,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.cpp")
 _LIB_PATH = os.path.join(_HERE, "_build", "libgs_oracle.so")
+# A prebuilt oracle library to load instead (the planted-mistake tests
+# point this at deliberately broken copies to show that the pins catch them).
+_LIB_OVERRIDE = os.environ.get("GS_ORACLE_LIB")
 _lib = None
 
 
@@ -48,8 +51,11 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_LIB_PATH)
+    if _LIB_OVERRIDE:
+        lib = ctypes.CDLL(_LIB_OVERRIDE)
+    else:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
     P = ctypes.c_void_p
     i64 = ctypes.c_int64
     ci = ctypes.c_int
@@ -77,6 +83,8 @@ def _load():
     lib.or_disconnected.restype = ci
     lib.or_connected_4pcf.argtypes = [P, P, P, P, P, P, P, P, P, ci]
     lib.or_connected_4pcf.restype = ci
+    lib.or_exact_to_double.argtypes = [P, ci]
+    lib.or_exact_to_double.restype = ctypes.c_double
     _lib = lib
     return lib
 
@@ -97,6 +105,18 @@ def quantize(pos, box_u: int, periodic: bool) -> np.ndarray:
     if st != 0:
         raise ValueError("coordinate outside the open box")
     return out
+
+
+def exact_to_double(value: int, scale: int) -> float:
+    """The oracle's final rounding step: the integer ``value`` (two's
+    complement, |value| < 2^255) times 2^-scale, rounded to the nearest
+    double with ties to even, as every exact weighted sum is rounded."""
+    v = int(value)
+    if not -(1 << 255) <= v < (1 << 255):
+        raise ValueError("value outside the 256-bit accumulator")
+    u = v & ((1 << 256) - 1)
+    words = np.array([(u >> (64 * k)) & ((1 << 64) - 1) for k in range(4)], dtype=np.uint64)
+    return float(_load().or_exact_to_double(_ptr(words), int(scale)))
 
 
 def num_configs(npoint: int, nb: int) -> int:

@@ -41,7 +41,7 @@
 // Weighted sums are accumulated exactly: every FP32 weight is an integer
 // multiple of a common power of two, products are formed in 128-bit
 // integers and summed in a 256-bit accumulator, and the exact total is
-// rounded to FP64 once at the end.
+// rounded to FP64 once at the end, to nearest with ties to even.
 //
 // Host threads partition hubs; each thread has its own histograms, summed
 // at the end (the shape of the paper's OpenMP CPU kernels, Sec. 4.3).
@@ -93,11 +93,27 @@ struct Acc256 {
       carry = c1 | c2;
     }
   }
-  // Value * 2^-scale as a double (truncated to 64 significant bits first).
+  // Bit k of the magnitude m (k outside [0, 256) reads as 0).
+  static unsigned bit_of(const uint64_t m[4], int k) {
+    if (k < 0 || k >= 256) return 0;
+    return (unsigned)((m[k >> 6] >> (k & 63)) & 1ull);
+  }
+  // Whether any bit of m below index k is set.
+  static bool any_below(const uint64_t m[4], int k) {
+    for (int q = 0; q < 256 && q < k; ++q)
+      if (bit_of(m, q)) return true;
+    return false;
+  }
+  // The value times 2^-scale, rounded to the nearest double with ties to
+  // even (IEEE 754 roundTiesToEven), taken straight from the definition:
+  // a double keeps the 53 leading bits of a normal number and, below
+  // 2^-1022, only the bits worth at least 2^-1074; the kept integer q is
+  // raised by one when the first dropped bit is 1 and either a later dropped
+  // bit is 1 or q is odd.
   double to_double(int scale) const {
     uint64_t m[4] = {w[0], w[1], w[2], w[3]};
-    bool neg = (m[3] >> 63) != 0;
-    if (neg) {  // two's complement negate
+    const bool neg = (m[3] >> 63) != 0;
+    if (neg) {  // magnitude of a negative two's-complement value
       unsigned carry = 1;
       for (int k = 0; k < 4; ++k) {
         uint64_t x = ~m[k];
@@ -106,25 +122,24 @@ struct Acc256 {
         m[k] = s;
       }
     }
-    int top = -1;
-    for (int k = 3; k >= 0; --k)
-      if (m[k]) { top = k; break; }
-    if (top < 0) return 0.0;
-    // take the top 64 significant bits
-    int lz = __builtin_clzll(m[top]);
-    int msb = top * 64 + (63 - lz);  // position of most significant bit
-    int shift = msb - 63;            // bits below the 64-bit window
-    uint64_t mant;
-    if (shift <= 0) {
-      mant = m[0];
-      shift = 0;
+    int lead = -1;  // index of the leading one bit
+    for (int k = 255; k >= 0; --k)
+      if (bit_of(m, k)) { lead = k; break; }
+    if (lead < 0) return 0.0;
+    // index of the last kept bit: 53 significant bits, or the 2^-1074 bit
+    // when the value lies below the smallest normal number
+    int cut = lead - 52;
+    if (lead - scale < -1022) cut = scale - 1074;
+    uint64_t q = 0;
+    for (int k = lead; k >= cut && k >= 0; --k) q = (q << 1) | bit_of(m, k);
+    if (cut > 0) {
+      const unsigned half = bit_of(m, cut - 1);
+      const bool rest = any_below(m, cut - 1);
+      if (half && (rest || (q & 1ull))) q += 1;
     } else {
-      int ws = shift / 64, bs = shift % 64;
-      uint64_t a = m[ws];
-      uint64_t b = (ws + 1 < 4) ? m[ws + 1] : 0;
-      mant = bs ? ((a >> bs) | (b << (64 - bs))) : a;
+      cut = 0;  // every bit kept: the value is a double exactly
     }
-    double v = std::ldexp((double)mant, shift - scale);
+    const double v = std::ldexp((double)q, cut - scale);  // q <= 2^53: exact
     return neg ? -v : v;
   }
 };
@@ -452,6 +467,15 @@ Conf4* conf4_cached(int nb) {
 
 // ============================================================================
 extern "C" {
+
+// Conversion of an exact 256-bit two's-complement integer (four 64-bit words,
+// least significant first) times 2^-scale to double, exposed for the pins of
+// the final rounding step.
+double or_exact_to_double(const uint64_t* words, int scale) {
+  Acc256 a;
+  for (int k = 0; k < 4; ++k) a.w[k] = words[k];
+  return a.to_double(scale);
+}
 
 // Sec. 2.1 input: float positions (h^-1 Mpc) -> int32 lattice coordinates.
 // Returns 0, or -1 when an open-box coordinate falls outside [0, box_u).

@@ -818,44 +818,47 @@ Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, bool comp
 
 }  // namespace
 
-// 192-bit two's-complement integer times 2^-scale, to double (the top 64
-// significant bits, then one rounding).
+// An exact 192-bit two's-complement sum times 2^-scale, rounded to the
+// nearest double with ties to even. The magnitude is first rounded to odd
+// at 64 significant bits (the dropped bits only force the lowest kept bit
+// to 1); the hardware's round-to-nearest conversion of that 64-bit integer
+// then gives the correctly rounded double, because rounding to odd with at
+// least two bits more than the target precision (64 >= 53 + 2) cannot make
+// the second rounding go wrong (S. Boldo, G. Melquiond, "Emulation of FMA
+// and correctly rounded sums: proved algorithms using rounding to odd",
+// IEEE Trans. Computers 57(4), 2008). The final power-of-two scaling is
+// exact: FP32 weights keep every scaled sum far above 2^-1022.
 __global__ void k_i192_to_double(const unsigned long long* acc, int64_t n, int scale,
                                  double* out) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long m[3] = {acc[3 * k], acc[3 * k + 1], acc[3 * k + 2]};
-    const bool neg = (m[2] >> 63) != 0;
-    if (neg) {
-      unsigned long long c = 1;
-      for (int q = 0; q < 3; ++q) {
-        const unsigned long long x = ~m[q];
-        const unsigned long long s = x + c;
-        c = (s < x) ? 1ull : 0ull;
-        m[q] = s;
-      }
+    unsigned long long a0 = acc[3 * k], a1 = acc[3 * k + 1], a2 = acc[3 * k + 2];
+    const bool neg = (long long)a2 < 0;
+    if (neg) {  // |value| = ~value + 1 across the three limbs
+      a0 = ~a0;
+      a1 = ~a1;
+      a2 = ~a2;
+      if (++a0 == 0ull && ++a1 == 0ull) ++a2;
     }
-    int top = -1;
-    for (int q = 2; q >= 0; --q)
-      if (m[q]) {
-        top = q;
-        break;
-      }
-    double v = 0.0;
-    if (top >= 0) {
-      const int msb = top * 64 + 63 - __clzll((long long)m[top]);
-      int shift = msb - 63;
-      unsigned long long mant;
-      if (shift <= 0) {
-        mant = m[0];
-        shift = 0;
-      } else {
-        const int ws = shift / 64, bs = shift % 64;
-        const unsigned long long lo = m[ws], hi = (ws + 1 < 3) ? m[ws + 1] : 0ull;
-        mant = bs ? ((lo >> bs) | (hi << (64 - bs))) : lo;
-      }
-      v = ldexp((double)mant, shift - scale);
+    unsigned long long top, lost;  // the 64-bit window and the bits below it
+    int below;                     // how many bits lie below the window
+    if (a2) {
+      const int z = __clzll((long long)a2);
+      top = z ? (a2 << z) | (a1 >> (64 - z)) : a2;
+      lost = (z ? a1 << z : a1) | a0;
+      below = 128 - z;
+    } else if (a1) {
+      const int z = __clzll((long long)a1);
+      top = z ? (a1 << z) | (a0 >> (64 - z)) : a1;
+      lost = z ? a0 << z : a0;
+      below = 64 - z;
+    } else {
+      top = a0;
+      lost = 0ull;
+      below = 0;
     }
+    top |= (lost != 0ull) ? 1ull : 0ull;  // round to odd
+    const double v = scalbn(__ull2double_rn(top), below - scale);
     out[k] = neg ? -v : v;
   }
 }
@@ -1062,9 +1065,9 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
 //
 // Some callers cannot let a library allocate device memory during a call:
 // code that runs under a fixed memory plan (a serving process that has
-// handed all of HBM to its own pool), real-time loops that must not hit the
-// allocator's locks or its implicit synchronisation, and code that records
-// its work for later replay and may not change the memory map meanwhile.
+// handed all of HBM to its own pool, so any further cudaMalloc fails), and
+// real-time loops that must not hit the allocator's locks or its implicit
+// device synchronisation.
 // For them gs_count_3pcf_noalloc counts the triangles of a resident graph
 // using only a fixed scratch array that lives in this library's device
 // image for as long as the library stays loaded (every GPU that loads the
@@ -1081,6 +1084,12 @@ namespace {
 constexpr int kNoAllocMaxBins = 35;
 constexpr size_t kNoAllocScratchBytes = 64 * 1024;
 constexpr size_t kNoAllocCountsOffset = 256;  // counter and error flag first
+constexpr size_t conf3_of(size_t nb) { return (nb + 2) * (nb + 1) * nb / 6; }
+// the counts of the largest bin count must fit behind the counter and flag
+static_assert(kNoAllocCountsOffset + 8 * conf3_of(kNoAllocMaxBins) <= kNoAllocScratchBytes,
+              "no-allocation scratch too small for kNoAllocMaxBins");
+static_assert(kNoAllocCountsOffset + 8 * conf3_of(kNoAllocMaxBins + 1) > kNoAllocScratchBytes,
+              "kNoAllocMaxBins is below what the scratch holds");
 }  // namespace
 }  // namespace gs
 
@@ -1123,7 +1132,10 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
   const Graph& g = G->g;
   if (!g.d_adj) return GS_EINVAL;  // out-of-core graphs need window buffers
   if (g.nb > kNoAllocMaxBins) return GS_ERANGE;
-  const Opts o = read_opts(options);
+  Opts o = read_opts(options);
+  // variant -1 means the tuned choice, as for gs_count_3pcf (a table lookup,
+  // no allocation)
+  o.variant = resolve_variant(g, 0, o.variant);
   cudaStream_t s = o.stream;
   const int nconf = (int)num_conf3(g.nb);
   void* scratch = nullptr;

@@ -1,9 +1,11 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
 Unweighted counts, pair counts and lattice coordinates must match bit for
-bit; weighted sums, xi and zeta_disc within 1e-12 relative (the oracle sums
-exactly; the GPU sums in FP64, or exactly with GS_FLAG_EXACT_WEIGHTS, and
-xi / zeta_disc differ only by FP64 evaluation order of RR).
+bit. Weighted sums must match bit for bit too: both sides sum exactly (as
+integers) and round the exact total once, to nearest with ties to even, by
+two independent conversions. xi and zeta_disc are compared within 1e-12
+relative: the two sides evaluate the analytic random pair counts RR with
+FP64 operations in different orders.
 """
 import json
 import math
@@ -167,7 +169,7 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     rc, rw = og.count_3pcf(w)
     gc, gw = run3(gs, torch_mod, X, bu, edges, w)
     assert np.array_equal(gc, rc)
-    np.testing.assert_allclose(gw, rw, rtol=RTOL, atol=0)
+    assert np.array_equal(gw, rw)
     # unweighted call on the same graph agrees with the weighted call's counts
     assert np.array_equal(run3(gs, torch_mod, X, bu, edges), rc)
     # every kernel path gives the same answer: hash path in 64-word segments
@@ -175,11 +177,11 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     g = gs.gs_build_graph(X, bu, edges)
     ex_c, ex_w = gs.gs_count_3pcf(g, w)
     assert np.array_equal(ex_c, rc)
-    np.testing.assert_allclose(ex_w, rw, rtol=RTOL)
+    assert np.array_equal(ex_w, rw)
     for variant in (1, 2, 4, 6, 8, 10, 32, 34, 36, 40, 64, 68, 72, 96):
         vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(vc, rc), variant
-        np.testing.assert_allclose(vw, gw, rtol=1e-13)
+        assert np.array_equal(vw, rw), variant
         # exact sums are identical bit for bit whichever path found them
         assert np.array_equal(gs.gs_count_3pcf(g, w, variant=variant)[1], ex_w)
 
@@ -202,9 +204,41 @@ def test_3pcf_signed_weights(gs, torch_mod):
     for variant in (0, 1, 4, 32, 64):
         gc, gw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(gc, rc), variant
-        np.testing.assert_allclose(gw, rw, rtol=RTOL, atol=0, err_msg=str(variant))
+        assert np.array_equal(gw, rw), variant
     _, gn = gs.gs_count_3pcf(g, -w)
     assert np.array_equal(gn, -gs.gs_count_3pcf(g, w)[1])
+
+
+def test_weighted_sum_rounds_to_nearest_at_a_tie(gs, torch_mod):
+    """One triangle (and one tetrahedron) whose weight product
+    (1 + 2^-23)^2 (1 + 2^-7 + 2^-23) has its bits at 2^0, -7, -22, -23, -29,
+    -45, -46, -53 and -69: the first dropped bit (2^-53) is set and a bit 16
+    places further down decides the rounding, so a conversion that kept only
+    the top 64 bits would see an exact tie and round down. The correctly
+    rounded sum rounds up; both sides must give exactly Fraction's value."""
+    from fractions import Fraction
+    a = np.float32(1 + 2.0 ** -23)
+    b = np.float32(1 + 2.0 ** -7 + 2.0 ** -23)
+    exact = Fraction(float(a)) ** 2 * Fraction(float(b))
+    truncated = float(Fraction(int(exact * 2 ** 63), 2 ** 63))
+    assert float(exact) != truncated
+    box_u = 100_000
+    edges = np.array([0, 100, 200], dtype=np.int64)
+    X = np.array([[500, 500, 500], [550, 500, 500], [500, 550, 500], [500, 500, 550]],
+                 dtype=np.int32)
+    for sign in (1.0, -1.0):
+        w3 = np.array([a, a, sign * b], dtype=np.float32)
+        c, ws = gs.gs_count_3pcf(gs.gs_build_graph(X[:3], box_u, edges), w3)
+        rc, rw = oracle.Graph(X[:3], box_u, edges).count_3pcf(w3)
+        assert c.sum() == 1 and np.array_equal(c, rc)
+        assert ws[c.argmax()] == sign * float(exact) and np.array_equal(ws, rw)
+        w4 = np.array([a, a, sign * b, 1.0], dtype=np.float32)
+        g4 = gs.gs_build_graph(X, box_u, edges)
+        e, o, we, wo = gs.gs_count_4pcf_parity(g4, w4)
+        re, ro, rwe, rwo = oracle.Graph(X, box_u, edges).count_4pcf(w4)
+        assert e.sum() == 1 and np.array_equal(e, re) and np.array_equal(o, ro)
+        assert we[e.argmax()] == sign * float(exact)
+        assert np.array_equal(we, rwe) and np.array_equal(wo, rwo)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
@@ -243,9 +277,9 @@ def test_3pcf_long_rows_segmented(gs, torch_mod, periodic):
     g = gs.gs_build_graph(dev(torch_mod, X), bu, edges)
     gc, gw = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1)
     assert np.array_equal(gc.cpu().numpy(), rc)
-    np.testing.assert_allclose(gw.cpu().numpy(), rw, rtol=RTOL)
+    assert np.array_equal(gw.cpu().numpy(), rw)
     _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w), variant=1)
-    np.testing.assert_allclose(gx.cpu().numpy(), rw, rtol=RTOL)
+    assert np.array_equal(gx.cpu().numpy(), rw)
 
 
 def test_3pcf_host_and_device_pointers(gs, torch_mod):
@@ -306,8 +340,7 @@ def test_4pcf_weighted(gs, torch_mod):
     re, ro, rwe, rwo = og.count_4pcf(w)
     ge, go, gwe, gwo = run4(gs, torch_mod, X, box_u, edges, w)
     assert np.array_equal(ge, re) and np.array_equal(go, ro)
-    np.testing.assert_allclose(gwe, rwe, rtol=RTOL)
-    np.testing.assert_allclose(gwo, rwo, rtol=RTOL, atol=1e-300)
+    assert np.array_equal(gwe, rwe) and np.array_equal(gwo, rwo)
 
 
 @pytest.mark.parametrize("periodic", [True, False])
@@ -471,10 +504,10 @@ def test_full_size_ddd_bit_exact(gs, torch_mod, ns1m):
     gc, gw = run3(gs, torch_mod, X, s["box_u"], s["edges_u"], w)
     assert rc.sum() > 1e9
     assert np.array_equal(gc, rc)
-    np.testing.assert_allclose(gw, rw, rtol=RTOL)
+    assert np.array_equal(gw, rw)
     g = gs.gs_build_graph(dev(torch_mod, X), s["box_u"], s["edges_u"])
     _, gx = gs.gs_count_3pcf(g, dev(torch_mod, w))
-    np.testing.assert_allclose(gx.cpu().numpy(), rw, rtol=RTOL)
+    assert np.array_equal(gx.cpu().numpy(), rw)
 
 
 def test_full_size_rrr_properties(gs, torch_mod):

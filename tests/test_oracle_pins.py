@@ -127,7 +127,8 @@ def test_3pcf_weighted_exact():
     g = oracle.Graph(X, box_u, edges_u, nthreads=2)
     c, ws = g.count_3pcf(w)
     assert np.array_equal(c, ref_c)
-    np.testing.assert_allclose(ws, ref_w, rtol=1e-15, atol=0)
+    # exact sums rounded once, to nearest: bit for bit the rational sums
+    assert np.array_equal(ws, ref_w)
     # unit weights reproduce the counts; doubling every weight scales by 8
     c1, w1 = g.count_3pcf(np.ones(X.shape[0], np.float32))
     assert np.array_equal(w1, c1.astype(np.float64))
@@ -148,7 +149,7 @@ def test_3pcf_signed_weights_exact():
     assert np.any(ref_w < 0) and np.any(ref_w > 0)
     c, ws = oracle.Graph(X, box_u, edges_u, nthreads=2).count_3pcf(w)
     assert np.array_equal(c, ref_c)
-    np.testing.assert_allclose(ws, ref_w, rtol=1e-15, atol=0)
+    assert np.array_equal(ws, ref_w)
 
 
 def test_3pcf_poisson_closed_form():
@@ -198,8 +199,7 @@ def test_4pcf_weighted_exact():
     g = oracle.Graph(X, box_u, edges_u)
     e, o, we, wo = g.count_4pcf(w)
     assert np.array_equal(e, e_ref) and np.array_equal(o, o_ref)
-    np.testing.assert_allclose(we, we_ref, rtol=1e-15)
-    np.testing.assert_allclose(wo, wo_ref, rtol=1e-15, atol=1e-300)
+    assert np.array_equal(we, we_ref) and np.array_equal(wo, wo_ref)
     _, _, we2, _ = g.count_4pcf(2 * w)
     assert np.array_equal(we2, 16 * we)
 
@@ -328,7 +328,7 @@ def test_pairs_match_all_pairs(periodic):
     g = oracle.Graph(X, bu, edges_u)
     p, wp = g.pairs(w)
     assert np.array_equal(p, ref)
-    np.testing.assert_allclose(wp, wref, rtol=1e-15)
+    assert np.array_equal(wp, wref)
 
 
 def test_disconnected_golden_two_bins():
