@@ -58,11 +58,13 @@ def parse():
                     help="launch variant bits for the --profile case (0 = the library default)")
     ap.add_argument("--no-next", action="store_true",
                     help="skip the connected 4pCF, equilateral and tooling measurements")
-    ap.add_argument("--mocks", type=int, default=0,
-                    help="also serve this many lognormal mock catalogues (request loop)")
+    ap.add_argument("--mocks", type=int, default=256,
+                    help="lognormal mock catalogues served through the request loop (0 = skip)")
     ap.add_argument("--mock-nmax", type=float, default=4e5)
-    ap.add_argument("--ooc", action="store_true",
-                    help="also measure the out-of-core overhead on the 1e6-point rmax-150 workload")
+    ap.add_argument("--mock-grid", type=int, default=256,
+                    help="Gaussian-field grid of the lognormal mocks (cells per side)")
+    ap.add_argument("--no-ooc", action="store_true",
+                    help="skip the out-of-core measurement on the 1e6-point rmax-150 workload")
     return ap.parse_args()
 
 
@@ -171,22 +173,64 @@ def load_workload(rank):
 # CPU oracle arm
 
 
-def oracle_rate(cats, box_u, edges, seconds, nthreads):
-    """Triangles/s of the oracle's 3pCF over the first hubs of the data
-    catalogue (query time only; its graph build is not timed)."""
-    import oracle
-    X = oracle.quantize(cats[0][0], box_u, True)
-    g = oracle.Graph(X, box_u, edges, nthreads=nthreads)
-    w = cats[0][1]
-    k = 2000
-    t0 = time.perf_counter()
-    c, _ = g.count_3pcf(w, hub_lo=0, hub_hi=k)
-    dt = time.perf_counter() - t0
-    k = int(min(X.shape[0], max(k, k * seconds / max(dt, 1e-3))))
-    t0 = time.perf_counter()
-    c, _ = g.count_3pcf(w, hub_lo=0, hub_hi=k)
-    dt = time.perf_counter() - t0
-    return float(c.sum()) / dt, k, dt, g
+# Stand-in for the 3e6 randoms in the oracle's sample: a uniform catalogue
+# at the same density (3e-3 per (h^-1 Mpc)^3) in a smaller periodic box,
+# whose hubs have the same neighbour statistics (building the oracle's
+# graph of all 3e6 randoms takes minutes and about 30 GB of host memory).
+RANDOMS_STANDIN_N = 300_000
+
+
+def randoms_standin():
+    spec = catalogs.WORKLOADS[WORKLOAD]
+    side = spec["box"] * (RANDOMS_STANDIN_N / spec["randoms"]) ** (1.0 / 3.0)
+    box_u = int(round(side * catalogs.LATTICE_PER_MPC))
+    side = box_u / catalogs.LATTICE_PER_MPC
+    pos = catalogs.uniform(RANDOMS_STANDIN_N, side, seed=spec["random_seed"] + 100)
+    w = catalogs.uniform_weights(RANDOMS_STANDIN_N, seed=spec["weight_seed"] + 100)
+    return pos, w, box_u, side
+
+
+class OracleMix:
+    """The oracle's 3pCF (counts + exact weighted sums) over the same
+    fraction f of the hubs of each catalogue of the step: hubs [0, f N_D) of
+    the 1e6-point data catalogue and f N_R hubs at the randoms' density. The
+    triangles counted over the time taken is the oracle's rate on the step's
+    own mix of clustered and uniform work. Graph builds are not timed."""
+
+    def __init__(self, cats, box_u, edges, nthreads):
+        import oracle
+        spec = catalogs.WORKLOADS[WORKLOAD]
+        self.nd, self.nr = spec["n"], spec["randoms"]
+        self.gd = oracle.Graph(oracle.quantize(cats[0][0], box_u, True), box_u, edges,
+                               nthreads=nthreads)
+        self.wd = cats[0][1]
+        pos, self.wr, rbox_u, self.rside = randoms_standin()
+        self.gr = oracle.Graph(oracle.quantize(pos, rbox_u, True), rbox_u, edges,
+                               nthreads=nthreads)
+        self.nthreads = nthreads
+        self.f = 1e-3
+
+    def run(self, f):
+        kd = max(1, int(f * self.nd))
+        kr = min(RANDOMS_STANDIN_N, max(1, int(f * self.nr)))
+        t0 = time.perf_counter()
+        cd, _ = self.gd.count_3pcf(self.wd, hub_lo=0, hub_hi=kd)
+        cr, _ = self.gr.count_3pcf(self.wr, hub_lo=0, hub_hi=kr)
+        dt = time.perf_counter() - t0
+        return float(cd.sum()) + float(cr.sum()), dt, kd, kr
+
+    def calibrate(self, seconds):
+        """Choose f so that one run takes about `seconds`."""
+        f = 2e-3
+        _, dt, _, _ = self.run(f)
+        self.f = min(RANDOMS_STANDIN_N / self.nr, max(1e-4, f * seconds / max(dt, 1e-3)))
+        return self.f
+
+    def sample(self, kd, kr):
+        return (f"oracle 3pCF (counts + exact weighted sums), same hub fraction of each catalogue: "
+                f"hubs [0, {kd}) of the 1e6-point Neyman-Scott data catalogue and [0, {kr}) of "
+                f"a {RANDOMS_STANDIN_N}-point uniform catalogue at the randoms' density (periodic "
+                f"L = {self.rside:.2f}); query time only")
 
 
 def run_reference(args):
@@ -197,33 +241,25 @@ def run_reference(args):
     spec, cats = load_workload(0)
     box_u, edges = spec["box_u"], spec["edges_u"]
     nthreads = oracle.default_threads()
-    X = oracle.quantize(cats[0][0], box_u, True)
-    g = oracle.Graph(X, box_u, edges, nthreads=nthreads)
-    w = cats[0][1]
+    mix = OracleMix(cats, box_u, edges, nthreads)
     # size one step to about budget / (steps + warmup) seconds
-    per_step = max(2.0, 150.0 / (args.steps + args.warmup))
-    k = 2000
-    t0 = time.perf_counter()
-    g.count_3pcf(w, hub_lo=0, hub_hi=k)
-    dt = time.perf_counter() - t0
-    k = int(min(X.shape[0], max(k, k * per_step / max(dt, 1e-3))))
+    f = mix.calibrate(max(2.0, 150.0 / (args.steps + args.warmup)))
     for _ in range(args.warmup):
-        g.count_3pcf(w, hub_lo=0, hub_hi=k)
-    tri, t0 = 0.0, time.perf_counter()
+        mix.run(f)
+    tri, dt = 0.0, 0.0
     for _ in range(args.steps):
-        c, _ = g.count_3pcf(w, hub_lo=0, hub_hi=k)
-        tri += float(c.sum())
-    dt = time.perf_counter() - t0
+        t, d, kd, kr = mix.run(f)
+        tri += t
+        dt += d
     value = tri / dt
-    sample = (f"oracle 3pCF (counts + exact weighted sums) over hubs [0, {k}) of the "
-              f"1e6-point Neyman-Scott data catalogue, query time only")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "hubs_per_step": k},
+            "config": {"workload": WORKLOAD, "hub_fraction": f, "data_hubs_per_step": kd,
+                       "random_hubs_per_step": kr},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": mix.sample(kd, kr)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -301,8 +337,10 @@ def run_ours(args):
     total_tri = float(tri_t.item()) * args.steps
     value = total_tri / (ms / 1e3)
 
-    # end to end through the public API: pinned host inputs copied in, the
-    # counts and weighted sums read back, every step
+    # End to end through the C ABI with HOST buffers: the pinned host
+    # positions go straight to gs_quantize (which copies them in), the
+    # pinned host weights to gs_count_3pcf, whose counts and weighted sums
+    # come back into pinned host arrays; every step.
     pinned = [(torch.from_numpy(p).pin_memory(), torch.from_numpy(w).pin_memory()) for p, w in cats]
     host_out = [(torch.empty(nconf, dtype=torch.uint64).pin_memory(),
                  torch.empty(nconf, dtype=torch.float64).pin_memory()) for _ in cats]
@@ -311,17 +349,15 @@ def run_ours(args):
 
     def step_e2e():
         for c, (pos_h, w_h) in enumerate(pinned):
-            pos = pos_h.to("cuda", non_blocking=True)
-            w = w_h.to("cuda", non_blocking=True)
-            x = gs.gs_quantize(pos, box_u, True, stream=stream)
-            g = gs.gs_build_graph(x, box_u, edges, stream=stream)
-            gs.gs_count_3pcf(g, w, counts=counts[c], wsum=wsums[c], stream=stream)
-            host_out[c][0].copy_(counts[c], non_blocking=True)
-            host_out[c][1].copy_(wsums[c], non_blocking=True)
+            gs.gs_quantize(pos_h, box_u, True, out=xyz[c], stream=stream)
+            g = gs.gs_build_graph(xyz[c], box_u, edges, stream=stream)
+            gs.gs_count_3pcf(g, w_h, counts=host_out[c][0], wsum=host_out[c][1], stream=stream)
             g.close()
-        torch.cuda.synchronize()
 
     step_e2e()
+    e2e_same = all(np.array_equal(host_out[c][0].numpy(), counts[c].cpu().numpy()) and
+                   np.array_equal(host_out[c][1].numpy(), wsums[c].cpu().numpy())
+                   for c in range(len(cats)))
     barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
@@ -334,19 +370,26 @@ def run_ours(args):
         torch.distributed.all_reduce(e_t, op=torch.distributed.ReduceOp.MAX)
     e2e_value = total_tri / float(e_t.item())
 
-    # roofline of the dominant kernel (RRR counting)
+    # Roofline of the dominant kernel (k_count3 on the randoms). Algorithmic
+    # bytes per launch, as the scope defines them: 5 bytes (a 4-byte id and a
+    # 1-byte bin) per edge for the hub rows once and for every spoke row
+    # N+(j) per hub-spoke edge: 5 (E + sum_(i,j) |N+(j)|). A stricter count
+    # (4-byte words, spoke rows only up to the merge-walk's exhaustion point)
+    # is reported beside it.
     peak, peak_kind = measured_peaks()
     bpe = info["bytes_per_edge"]
-    alg_bytes = bpe * (info["edges"] + info["walk_words"])
+    alg_bytes = 5 * (info["edges"] + info["probe_words"])
+    strict_bytes = bpe * (info["edges"] + info["walk_words"])
     k_ms = float(np.mean(kernel_ms)) if kernel_ms else float("nan")
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
     traffic = recorded_traffic()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-            "limiter": "instruction issue (ncu: 77% of issue slots busy, integer ALU pipe 59%, "
-                       "L1/shared pipe 71%, L2 hit 98.9%, DRAM 0.09%): spoke rows are re-read "
-                       "from L2",
+            "per_unit": "5 B per edge of the hub row and of every spoke row N+(j)",
+            "limiter": "instruction issue (spoke rows are re-read from L2, not HBM)",
             "kernel": "k_count3 (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+            "strict_bytes_per_launch": strict_bytes,
+            "strict_frac": strict_bytes / (k_ms / 1e3) / 1e9 / peak,
             "triangles_per_launch": float(counts[1].sum().item())}
 
     if rank != 0:
@@ -355,17 +398,22 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         nthreads = oracle.default_threads()
-        rate, k, dt, _ = oracle_rate(cats, box_u, edges, args.cpu_seconds, nthreads)
-        cpu = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-               "sample": f"oracle 3pCF (counts + exact weighted sums) over hubs [0, {k}) of the "
-                         f"1e6-point data catalogue, query time only ({dt:.1f} s)"}
+        mix = OracleMix(cats, box_u, edges, nthreads)
+        f = mix.calibrate(args.cpu_seconds)
+        tri_cpu, dt_cpu, kd, kr = mix.run(f)
+        cpu = {"value": tri_cpu / dt_cpu, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": mix.sample(kd, kr) + f" ({dt_cpu:.1f} s)"}
+        del mix
     clocks = clk.summary()
     quad = None
     if not args.no_4pcf:
         quad = measure_4pcf(gs, torch)
     nxt = None if args.no_next else measure_next(gs, torch, dev[1], box_u, edges, k_ms)
-    mocks = measure_mocks(gs, torch, args.mocks, args.mock_nmax) if args.mocks else None
-    ooc = measure_ooc(gs, torch) if args.ooc else None
+    del dev
+    torch.cuda.empty_cache()
+    ooc = None if args.no_ooc else measure_ooc(gs, torch)
+    mocks = measure_mocks(gs, torch, args.mocks, args.mock_nmax, args.mock_grid) \
+        if args.mocks else None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -379,7 +427,8 @@ def run_ours(args):
             "triangles_per_step": tri_step,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "results_identical": bool(e2e_same),
+                    "path": "pinned host positions, weights and outputs passed to the C ABI"},
             "gpu_launches": int(launches), "clocks": clocks, "quadruplets": quad,
             "mocks": mocks, "out_of_core": ooc, "next_rows": nxt,
             "graph_randoms": {k2: info[k2] for k2 in ("edges", "max_degree", "probe_words",
@@ -389,7 +438,11 @@ def run_ours(args):
 
 def measure_4pcf(gs, torch, runs=2):
     """Quadruplets/s of the parity 4pCF on 2e5 Neyman-Scott points (L=400,
-    rmax 30 in 8 bins), plus the pair sweep and disconnected term."""
+    rmax 30 in 8 bins), plus the pair sweep and disconnected term, with the
+    roofline of the counting kernel: algorithmic bytes per launch
+    B4 = 5 (E + sum_(i,j) |N+(j)| + sum_(triangles i<j<k) |N+(k)|), the 3pCF
+    walk plus the row of every triangle's third vertex that the three-way
+    merge of Eq. threeway reads."""
     spec = catalogs.draw("ns200k_L400_r30_nb8")
     box_u, edges = spec["box_u"], spec["edges_u"]
     pos = torch.from_numpy(spec["pos"]).cuda()
@@ -398,7 +451,7 @@ def measure_4pcf(gs, torch, runs=2):
     gs.gs_count_4pcf_parity(g, like=like)
     import ctypes
     km = ctypes.c_double(0.0)
-    ms = []
+    ms, kms = [], []
     for _ in range(runs):
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -407,17 +460,30 @@ def measure_4pcf(gs, torch, runs=2):
         t1.record()
         torch.cuda.synchronize()
         ms.append(t0.elapsed_time(t1))
+        kms.append(km.value)
     tet = float(even.sum().item())
     pk = ctypes.c_double(0.0)
     gs.gs_disconnected_4pcf(g, like=like, kernel_ms=pk)
     info = gs.gs_graph_info(g)
+    tri, tail = gs.gs_graph_tri_words(g)
     g.close()
     best = min(ms)
+    k_ms = min(kms)
+    peak, peak_kind = measured_peaks()
+    b4 = 5 * (info["edges"] + info["probe_words"] + tail)
+    achieved = b4 / (k_ms / 1e3) / 1e9
     return {"workload": "ns200k_L400_r30_nb8", "metric": "binned quadruplets/s (4pCF even+odd)",
             "value": tet / (best / 1e3), "unit": "quadruplets/s", "tetrahedra": tet,
-            "call_ms": best, "kernel_ms": km.value, "pair_sweep_ms": pk.value,
+            "triangles": tri, "call_ms": best, "kernel_ms": k_ms, "pair_sweep_ms": pk.value,
             "pair_sweep_gbs": info["edge_slots"] * 4 / (pk.value / 1e3) / 1e9 if pk.value else None,
-            "odd_abs_sum": float(odd.abs().sum().item())}
+            "odd_abs_sum": float(odd.abs().sum().item()),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_count4 (parity)", "alg_bytes_per_launch": b4,
+                         "per_unit": "5 B per edge: hub rows, spoke rows, and the row of each "
+                                     "triangle's third vertex",
+                         "limiter": "instruction issue on shared-memory bit rows (the rows of "
+                                    "a hub's neighbourhood are staged once per hub)"}}
 
 
 def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
@@ -485,45 +551,59 @@ def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
     return out
 
 
-def make_mocks(count, nmax, seed=11):
+def _one_mock(args):
+    n, L, seed, grid = args
+    return catalogs.lognormal(int(n), L, seed=seed, grid=grid)
+
+
+def make_mocks(count, nmax, grid, seed=11):
     """Lognormal mock ensemble: sizes log-uniform in [5e4, nmax], L = 500,
-    3pCF rmax 60 in 12 bins; the first 32 also ask for the 4pCF (rmax 25,
-    6 bins). A 128^3 field keeps host generation to a fraction of a second
-    per catalogue."""
+    each catalogue drawn from its own Gaussian field on a grid^3 mesh
+    (P(k) ~ k^-1.5, 2 h^-1 Mpc smoothing). Generated on the host in a pool
+    of fresh (spawned) worker processes."""
+    import multiprocessing as mp
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = np.exp(rng.uniform(np.log(5e4), np.log(nmax), size=count)).astype(int)
     L = 500.0
-    out = []
-    for k, n in enumerate(sizes):
-        pos = catalogs.lognormal(int(n), L, seed=seed * 1000 + k, grid=128)
-        out.append(pos)
+    jobs = [(int(n), L, seed * 1000 + k, grid) for k, n in enumerate(sizes)]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        out = pool.map(_one_mock, jobs, chunksize=1)
     return out, sizes, L
 
 
-def measure_mocks(gs, torch, count, nmax):
+def measure_mocks(gs, torch, count, nmax, grid):
+    """The mock-ensemble campaign: 3pCF (rmax 60, 12 bins) of every
+    catalogue and, for the first 32, the parity 4pCF (rmax 25, 6 bins).
+    (a) one catalogue at a time through the plain API (build, count, free);
+    (b) the request loop with every request submitted at once (saturated:
+    its throughput is the capacity); (c) the request loop under Poisson
+    arrivals at 0.8x that capacity (latency arrival -> result)."""
     L = 500.0
     box_u = int(L * 1024)
     e3 = catalogs.bin_edges_u(0.0, 60.0, 12)
     e4 = catalogs.bin_edges_u(0.0, 25.0, 6)
     t_gen = time.perf_counter()
-    mocks, sizes, _ = make_mocks(count, nmax)
+    mocks, sizes, _ = make_mocks(count, nmax, grid)
     t_gen = time.perf_counter() - t_gen
     xyz = [gs.gs_quantize(p, box_u, True) for p in mocks]
+    del mocks
     kinds = [4 if k < 32 else 3 for k in range(count)]
     # a) one catalogue at a time through the plain API
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain = []
+    plain, plain4 = [], {}
     for k, X in enumerate(xyz):
         g = gs.gs_build_graph(X, box_u, e3)
         plain.append(gs.gs_count_3pcf(g))
         g.close()
         if kinds[k] == 4:
             g4 = gs.gs_build_graph(X, box_u, e4)
-            gs.gs_count_4pcf_parity(g4)
+            plain4[k] = gs.gs_count_4pcf_parity(g4)
             g4.close()
     t_plain = time.perf_counter() - t0
     tri = float(sum(int(c.sum()) for c in plain))
+    tet = float(sum(int(e.sum()) for e, _ in plain4.values()))
 
     def serve(rate):
         lat, res = [], {}
@@ -540,18 +620,24 @@ def measure_mocks(gs, torch, count, nmax):
             for k, t in tickets:
                 c, o, ws, info = srv.wait(t)
                 lat.append(info["t_done"] - info["t_submit"])
-                res[k] = c
+                res[k] = (c, o)
             span = time.perf_counter() - t_start
         return span, np.array(lat), res
 
+    def identical(res):
+        ok = all(np.array_equal(res[k][0], plain[k]) for k in range(count))
+        return ok and all(np.array_equal(res[-1 - k][0], e) and np.array_equal(res[-1 - k][1], o)
+                          for k, (e, o) in plain4.items())
+
     t_sat, lat_sat, res = serve(0.0)
-    same = all(np.array_equal(res[k], plain[k]) for k in range(count))
+    same = identical(res)
     capacity = count / t_sat
     t_poi, lat_poi, res2 = serve(0.8 * capacity)
-    same = same and all(np.array_equal(res2[k], plain[k]) for k in range(count))
+    same = same and identical(res2)
     return {"catalogues": count, "n_range": [int(sizes.min()), int(sizes.max())],
+            "points": int(sizes.sum()), "grid": grid,
             "box": L, "rmax3": 60.0, "nb3": 12, "rmax4": 25.0, "nb4": 6, "also_4pcf": min(32, count),
-            "triangles": tri, "host_generation_s": t_gen,
+            "triangles": tri, "tetrahedra": tet, "host_generation_s": t_gen,
             "one_at_a_time_s": t_plain, "one_at_a_time_catalogues_per_s": count / t_plain,
             "served_saturated_s": t_sat, "served_catalogues_per_s": capacity,
             "speedup_vs_one_at_a_time": t_plain / t_sat,

@@ -149,6 +149,17 @@ int gs_build_graph(const int32_t* xyz, int64_t n, int64_t box_u, const int64_t* 
 int gs_graph_info(const gs_graph* g, gs_graph_stats* stats);
 
 /*
+ * gs_graph_tri_words - statistics of the triangle walk that bound the
+ * 4-point query's memory traffic (the three-way merge of Eq. threeway reads,
+ * for every triangle i < j < k, the row N+(k) of its largest vertex):
+ *   *triangles   number of triangles (every configuration together);
+ *   *tail_words  sum over those triangles of |N+(k)|.
+ * Host pointers. Runs a plain binary-search walk over the graph (seconds
+ * for graphs of about 1e8 edges). Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA.
+ */
+int gs_graph_tri_words(const gs_graph* g, int64_t* triangles, int64_t* tail_words);
+
+/*
  * gs_graph_export - copy the oriented CSR out, in the graph's own labels.
  *   ptr  int64 [n+1]: row i holds N+(i) = {j > i adjacent to i} in
  *        nbr[ptr[i] .. ptr[i]+deg(i)) in ascending order (rows are padded,

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
-    "gs_graph_info", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_3pcf_equilateral", "gs_count_4pcf",
+    "gs_graph_info", "gs_graph_tri_words", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_3pcf_equilateral", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_config_mask_cm",
     "gs_rebin_3pcf", "gs_rebin_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
@@ -82,6 +82,7 @@ def _load():
         "gs_build_graph": ([P, i64, i64, P, ci, OP, ctypes.POINTER(P)], ci),
         "gs_graph_info": ([P, ctypes.POINTER(GraphStats)], ci),
         "gs_graph_export": ([P, P, P, P, P, P], ci),
+        "gs_graph_tri_words": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ci),
         "gs_count_3pcf": ([P, P, P, P, OP], ci),
         "gs_count_4pcf": ([P, P, P, P, OP], ci),
         "gs_count_3pcf_batch": ([P, ctypes.c_int32, P, P, P, OP], ci),
@@ -241,6 +242,15 @@ def gs_graph_info(g: Graph) -> dict:
     s = GraphStats()
     _check(_lib.gs_graph_info(g.handle, ctypes.byref(s)), "gs_graph_info")
     return s.as_dict()
+
+
+def gs_graph_tri_words(g: Graph):
+    """(triangles, sum over triangles i<j<k of |N+(k)|) of the graph."""
+    t = ctypes.c_int64(0)
+    w = ctypes.c_int64(0)
+    _check(_lib.gs_graph_tri_words(g.handle, ctypes.byref(t), ctypes.byref(w)),
+           "gs_graph_tri_words")
+    return int(t.value), int(w.value)
 
 
 def gs_graph_export(g: Graph):

@@ -575,6 +575,11 @@ int gs_graph_info(const gs_graph* G, gs_graph_stats* s) {
   return GS_OK;
 }
 
+int gs_graph_tri_words(const gs_graph* G, int64_t* triangles, int64_t* tail_words) {
+  if (!G || !triangles || !tail_words) return GS_EINVAL;
+  return tri_words_device(G->g, triangles, tail_words);
+}
+
 uint64_t gs_kernel_launches(void) { return g_launches.load(); }
 
 namespace gs {

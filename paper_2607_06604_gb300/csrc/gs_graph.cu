@@ -500,6 +500,75 @@ __global__ void k_walk_words(const int32_t* __restrict__ deg, const int64_t* __r
 }
 }  // namespace
 
+namespace {
+// Triangles (i < j < k) and the sum over them of |N+(k)|: one warp per hub,
+// lanes over the words of each spoke row N+(j); a word k is a triangle when
+// a binary search finds it in N+(i).
+__global__ void k_tri_words(const int32_t* __restrict__ deg, const int64_t* __restrict__ ptr,
+                            const uint32_t* __restrict__ adj, int64_t adj_off, int64_t split,
+                            int64_t adj_off2, int64_t h0, int64_t h1, unsigned long long* tri,
+                            unsigned long long* words) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long nt = 0, nw = 0;
+  for (int64_t i = h0 + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < h1;
+       i += warps) {
+    const int d = deg[i];
+    if (d < 2) continue;
+    const uint32_t* r = row_at(adj, ptr, i, adj_off, split, adj_off2);
+    for (int s = 0; s + 1 < d; ++s) {
+      const uint32_t j = edge_id(r[s]);
+      const uint32_t* rj = row_at(adj, ptr, j, adj_off, split, adj_off2);
+      const int dj = deg[j];
+      for (int t = lane; t < dj; t += 32) {
+        const uint32_t k = edge_id(rj[t]);
+        int lo = s + 1, hi = d;  // k > j, so only the hub row after j
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (edge_id(r[mid]) < k) lo = mid + 1;
+          else hi = mid;
+        }
+        if (lo < d && edge_id(r[lo]) == k) {
+          nt += 1;
+          nw += (unsigned long long)deg[k];
+        }
+      }
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    nt += __shfl_xor_sync(0xffffffffu, nt, o);
+    nw += __shfl_xor_sync(0xffffffffu, nw, o);
+  }
+  if (lane == 0) {
+    atomicAdd(tri, nt);
+    atomicAdd(words, nw);
+  }
+}
+}  // namespace
+
+int tri_words_device(const Graph& g, int64_t* tri, int64_t* words) {
+  *tri = *words = 0;
+  if (g.n == 0 || g.slots == 0) return GS_OK;
+  Opts o;
+  Scratch sc(o.stream);
+  unsigned long long* tot = sc.alloc<unsigned long long>(2);
+  if (!tot) return GS_ENOMEM;
+  cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), o.stream);
+  int st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+    { k_tri_words<<<grid_blocks((v.h1 - v.h0) * 32, 256), 256, 0, o.stream>>>(
+        g.d_deg, g.d_ptr, v.adj, v.off1, v.split, v.off2, v.h0, v.h1, tot, tot + 1); note_launch(); }
+    return cuda_status(cudaGetLastError());
+  });
+  if (st) return st;
+  unsigned long long h[2] = {0, 0};
+  cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, o.stream);
+  cudaError_t e = cudaStreamSynchronize(o.stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  *tri = (int64_t)h[0];
+  *words = (int64_t)h[1];
+  return GS_OK;
+}
+
 int walk_words_device(Graph* g) {
   if (g->n == 0 || g->slots == 0) {
     g->walk_words = 0;

@@ -172,6 +172,7 @@ int connected_device(const Graph& gdr, const FixedW& fdr, const Graph& gr, const
                      double* d_xi, double* d_even, double* d_odd, double* d_disc, double* d_conn,
                      const Opts& o, Scratch& sc);
 int walk_words_device(Graph* g);
+int tri_words_device(const Graph& g, int64_t* tri, int64_t* words);
 int quantize_device(const double* d_pos, int64_t n, int64_t box_u, int periodic, int32_t* d_xyz,
                     cudaStream_t s, Scratch& sc);
 

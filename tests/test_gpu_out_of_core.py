@@ -40,11 +40,19 @@ def resident(gs, case):
            "c4": gs.gs_count_4pcf_parity(g),
            "pairs": gs.gs_disconnected_4pcf(g, w), "export": gs.gs_graph_export(g),
            "info": gs.gs_graph_info(g)}
-    # the resident path itself is pinned to the oracle
+    # the resident path itself is pinned to the oracle: 3pCF counts and
+    # exact weighted sums, 4pCF even and odd channels, weighted pair sums,
+    # so every windowed result compared with it below is compared with the
+    # oracle too
     og = oracle.Graph(X, box_u, edges)
     rc, rw = og.count_3pcf(w)
     assert np.array_equal(out["c3"][0], rc)
     assert np.array_equal(out["c3"][1], rw)
+    re, ro = og.count_4pcf()
+    assert re.sum() > 0 and np.array_equal(out["c4"][0], re) and np.array_equal(out["c4"][1], ro)
+    rp, rxi, _ = og.disconnected(w)
+    assert np.array_equal(out["pairs"][0], rp)
+    np.testing.assert_allclose(out["pairs"][1], rxi, rtol=1e-12, atol=1e-12)
     return out
 
 
