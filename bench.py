@@ -82,7 +82,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_VERSION = "k_count3.v13"  # bump when k_count3 changes; stale captures then report null
+KERNEL_VERSION = "k_count3p.v1"  # bump when k_count3 changes; stale captures then report null
 
 
 def recorded_traffic():
@@ -386,8 +386,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
             "per_unit": "5 B per edge of the hub row and of every spoke row N+(j)",
-            "limiter": "instruction issue (spoke rows are re-read from L2, not HBM)",
-            "kernel": "k_count3 (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+            "limiter": "shared-memory pipe (pair tests on staged neighbours, histogram atomics)",
+            "kernel": "k_count3p (RRR)", "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
             "strict_bytes_per_launch": strict_bytes,
             "strict_frac": strict_bytes / (k_ms / 1e3) / 1e9 / peak,
             "triangles_per_launch": float(counts[1].sum().item())}

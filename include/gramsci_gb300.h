@@ -65,10 +65,13 @@ typedef struct {
   /* > 0 forces that many row windows (out-of-core mode even when the
    * graph fits); 0 = automatic. */
   int32_t force_windows;
-  /* Kernel variant bits: 0 = automatic. 1 = exercise the long-row code
-   * paths on any input (gs_count_3pcf probes a hash of the hub row staged
-   * in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
-   * global memory). 2 = gs_count_3pcf reads hub rows from global memory
+  /* Kernel variant bits: 0 = automatic (gs_count_3pcf tests every pair of
+   * a hub's neighbours geometrically; see gs_count_3pcf). 512 = gs_count_3pcf
+   * uses the merge-walk kernel of Sec. 3.1 instead, as does any of the bits
+   * 1, 2, 8, 16, 32 and 64, which select its paths. 1 = exercise the
+   * long-row code paths on any input (the walk probes a hash of the hub row
+   * staged in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
+   * global memory). 2 = the walk reads hub rows from global memory
    * instead of staging them. 4 = gs_count_3pcf computes configuration
    * indices instead of looking them up in a shared table, and
    * gs_count_4pcf* bins the non-hub edges by binary search over the bin
@@ -172,8 +175,12 @@ int gs_graph_export(const gs_graph* g, int64_t* ptr, int32_t* deg, int32_t* nbr,
                     int32_t* perm);
 
 /*
- * gs_count_3pcf - binned triangle counts (Sec. 2.2) found with a
- * hub-and-spoke intersection of sorted rows (Sec. 3.1).
+ * gs_count_3pcf - binned triangle counts (Sec. 2.2). Every triangle i<j<k
+ * is found at its smallest vertex i from the pair (j, k) of N+(i); the
+ * default kernel decides whether (j, k) is an edge from the exact lattice
+ * distance of the pair, the merge-walk kernel (variant bit 512) by the
+ * hub-and-spoke intersection of sorted rows of Sec. 3.1. Both give the
+ * same counts and sums.
  *   w       NULL (unweighted) or float32 [n] weights in caller order.
  *   counts  uint64 [C(nb+2,3)] triangle counts per configuration.
  *   wsum    NULL or float64 [C(nb+2,3)]: sum of w_i w_j w_k per

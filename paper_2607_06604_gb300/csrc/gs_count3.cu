@@ -1,24 +1,33 @@
-// Binned triangle counts (Sec. 2.2) with the hub-and-spoke intersection of
-// sorted rows (Sec. 3.1), GB300 layout.
+// Binned triangle counts (Sec. 2.2), GB300 layout. Two kernels give the same
+// counts and exact weighted sums:
 //
-// For each hub i and spoke j in N+(i), the triangles (i, j, k) with k > j
-// are k in N+(i) intersected with N+(j). The paper walks both sorted lists
-// with two pointers; here one persistent 1024-thread CTA per SM takes one
-// hub at a time and stages N+(i) in shared memory with a bulk (TMA) copy.
-// Because ids are cell ordered, N+(i) lies in a short id span above i, so
-// the CTA writes every neighbour's bin into a shared byte table indexed by
-// id - (i + 1) (0xFF = not a neighbour). Each warp then streams the row
-// N+(j) of one spoke at a time with 128-bit loads (four edge words per
-// lane) and probes the table with one subtraction and one byte load; a
-// spoke row is abandoned as soon as its ids pass the largest id of N+(i)
-// (the merge-walk's exhaustion rule). Only the entries written are reset
-// afterwards. Hubs whose span exceeds the table (wrap-around neighbours of
-// a periodic box, very sparse catalogues) use a shared hash of N+(i) in
-// the same memory, staged in segments.
-// The configuration index comes from a shared table over (b_ij, b_ik, b_jk);
-// counts go to per-CTA shared-memory histograms flushed with one 64-bit
-// atomic per bin. Weighted sums use exact fixed point: 128-bit products in
-// shared 128-bit accumulators, flushed into 192-bit global accumulators.
+// k_count3p (the default): every triangle i < j < k is found at its smallest
+// vertex i from the pair (j, k) of N+(i). The CTA stages the hub-relative
+// displacement of every neighbour and tests each pair of N+(i) directly: it
+// is an edge exactly when its lattice distance lies in [E_0, E_nb), and the
+// bin comes from the same squared distance. No spoke row is read; the work
+// is C(|N+(i)|, 2) integer distance tests per hub on shared-memory operands.
+//
+// k_count3 (the merge-walk of Sec. 3.1): for each hub i and spoke j in N+(i),
+// the triangles (i, j, k) with k > j are k in N+(i) intersected with N+(j).
+// The paper walks both sorted lists with two pointers; here one persistent
+// 1024-thread CTA per SM takes one hub at a time and stages N+(i) in shared
+// memory with a bulk (TMA) copy. Because ids are cell ordered, N+(i) lies in
+// a short id span above i, so the CTA writes every neighbour's bin into a
+// shared byte table indexed by id - (i + 1) (0xFF = not a neighbour). Each
+// warp then streams the row N+(j) of one spoke at a time with 128-bit loads
+// (four edge words per lane) and probes the table with one subtraction and
+// one byte load; a spoke row is abandoned as soon as its ids pass the
+// largest id of N+(i) (the merge-walk's exhaustion rule). Only the entries
+// written are reset afterwards. Hubs whose span exceeds the table
+// (wrap-around neighbours of a periodic box, very sparse catalogues) use a
+// shared hash of N+(i) in the same memory, staged in segments.
+//
+// Both: the configuration index comes from a shared table over (b_ij, b_ik,
+// b_jk); counts go to per-CTA shared-memory histograms flushed with one
+// 64-bit atomic per bin. Weighted sums use exact fixed point: per hub, 96-bit
+// sums of W_j W_k kept in 32-bit limbs, multiplied by W_i into the CTA's
+// 128-bit sums, flushed into 192-bit global accumulators.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -49,6 +58,8 @@ struct Cat {
   unsigned long long* counts;  // [nconf]
   unsigned long long* wacc;    // [nconf][3] 192-bit weighted sums
   int64_t hub_begin, hub_end;
+  const int4* __restrict__ xyzp;  // (x, y, z, caller index) in internal order
+  int64_t box;                    // periodic side in lattice units, 0 = open box
 };
 
 struct Args {
@@ -774,6 +785,375 @@ void (*pick_equi3(int wm, bool nonneg, bool smem_hist))(Args) {
                 : k_count3<kExact, true, false, false, true>;
 }
 
+// ----------------------------------------------------------------------------
+// Pair-geometry triangle counting (the default launch).
+//
+// Every triangle i < j < k has j and k in N+(i). The walk above finds the
+// pairs (j, k) of N+(i) that are edges by intersecting sorted rows; this
+// kernel tests the pairs directly. The CTA stages, for every neighbour of
+// the hub, its minimum-image displacement D from the hub (exact lattice
+// integers) and the hub edge's bin; then every pair (j, k) of N+(i) with
+// j < k is an edge exactly when E_0^2 <= |D_k - D_j|^2 < E_nb^2 (in a
+// periodic box 4 E_nb < L makes D_k - D_j the minimum image of k - j), and
+// its bin follows from the same squared distance. No spoke row is read:
+// the work per hub is C(d, 2) integer distance tests on shared-memory
+// operands, and a hit is recorded exactly as in the walk (per-CTA 32-bit
+// histograms, per-hub 96-bit sums of W_j W_k folded by W_i).
+constexpr int kPThreads = 512;
+constexpr int kPBucketMax = 2048;         // buckets no wider than the narrowest bin
+constexpr int kPBucketExactMax = 16384;  // buckets that each hold one bin
+
+// Shared-memory updates on 32-bit shared addresses, done only when pred
+// holds (no branch): the pair kernel records every examined pair's update
+// under its hit predicate, so the warp never diverges on a hit.
+__device__ inline void red_add_shared_if(uint32_t a, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t"
+      "@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(a),
+      "r"(v), "r"((uint32_t)pred)
+      : "memory");
+}
+__device__ inline uint32_t atom_add_shared_if(uint32_t a, uint32_t v, bool pred) {
+  uint32_t old = 0u;  // stays 0 when pred is false
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+      "@p atom.shared.add.u32 %0, [%1], %2;\n\t}"
+      : "+r"(old)
+      : "r"(a), "r"(v), "r"((uint32_t)pred)
+      : "memory");
+  return old;
+}
+
+// One pair's count and, weighted, W_j W_k into the hub's 96-bit limbs
+// (hist and hacc as shared addresses), when hit holds.
+template <int WM>
+__device__ inline void record_if(uint32_t hist, uint32_t hacc, int cf, bool hit, int32_t Wj,
+                                 int32_t Wk) {
+  red_add_shared_if(hist + 4u * (uint32_t)cf, 1u, hit);
+  if constexpr (WM >= kExact) {
+    const long long x = (long long)Wj * Wk;
+    const uint32_t x0 = (uint32_t)x;
+    const uint32_t x1 = (uint32_t)((unsigned long long)x >> 32);
+    const uint32_t lo = hacc + 12u * (uint32_t)cf;
+    const uint32_t o0 = atom_add_shared_if(lo, x0, hit);
+    const uint32_t a1 = x1 + ((o0 + x0 < o0) ? 1u : 0u);
+    if constexpr (WM == kExactPos) {
+      // 0 <= x < 2^60: x1 + carry cannot wrap; the top limb only takes the
+      // mid limb's carries
+      const uint32_t o1 = atom_add_shared_if(lo + 4u, a1, hit);
+      red_add_shared_if(lo + 8u, 1u, hit && (o1 + a1 < o1));
+    } else {
+      uint32_t a2 = (x < 0 ? 0xFFFFFFFFu : 0u) + ((a1 < x1) ? 1u : 0u);
+      const uint32_t o1 = atom_add_shared_if(lo + 4u, a1, hit && a1 != 0u);
+      a2 += (o1 + a1 < o1) ? 1u : 0u;
+      red_add_shared_if(lo + 8u, a2, hit && a2 != 0u);
+    }
+  }
+}
+
+struct PArgs {
+  Cat one;              // single-catalogue launches
+  const Cat* cats;      // batched launches (catalogues with equal bin edges)
+  const int64_t* base;
+  int ncats;
+  int nb, nconf;
+  int cap;              // neighbours staged in shared memory
+  int use_lut;
+  int bk_shift, bk_n;   // squared-distance buckets (bk_n = 0: binary search)
+  const int64_t* e2g;   // nb + 1 squared bin edges
+  unsigned char* gscratch;  // hubs above cap: per-CTA staging in global memory
+  size_t gstride;
+  unsigned long long* hub_counter;
+  float lin_c;          // linear bins: 1 / m, raised by 2^-20 (see the pair test)
+};
+
+__device__ inline int64_t min_image(int64_t d, int64_t box) {
+  if (box) {
+    if (2 * d >= box) d -= box;
+    else if (2 * d < -box) d += box;
+  }
+  return d;
+}
+
+// Binning of a pair's squared distance D2 in the pair kernel.
+enum : int {
+  kBinSearch = 0,  // range test, then buckets finished by one comparison (or a search)
+  kBinTable = 1,   // every squared edge is a multiple of the bucket width: one lookup
+  kBinLinear = 2   // E_b = b m 2^t, E_0 = 0: the bin is floor(sqrt(D2 / 2^2t) / m)
+};
+
+template <int WM, bool BATCH, bool LUT, int BIN>
+__global__ void __launch_bounds__(kPThreads, 2) k_count3p(PArgs a) {
+  constexpr bool WEIGHTED = WM != kNone;
+  using WT = WType<WM>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nb = a.nb;
+  Smem sm;
+  int4* s_stage;
+  int64_t* s_e2;
+  uint8_t* s_bk;
+  {
+    unsigned char* p = smem;
+    s_stage = reinterpret_cast<int4*>(p);
+    p += (size_t)a.cap * 16;
+    s_e2 = reinterpret_cast<int64_t*>(p);
+    p += (size_t)(nb + 1) * 8;
+    p = reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    const int nb3 = nb * nb * nb;
+    sm.lut = LUT ? reinterpret_cast<uint16_t*>(p) : nullptr;
+    if (LUT) p += ((nb3 * 2 + 15) / 16) * 16;
+    sm.hist = reinterpret_cast<unsigned*>(p);
+    p += ((a.nconf * 4 + 15) / 16) * 16;
+    sm.whist = reinterpret_cast<unsigned long long*>(p);
+    sm.hacc = reinterpret_cast<unsigned*>(sm.whist + 2 * a.nconf);
+    if (WEIGHTED) p += (size_t)a.nconf * 28;
+    s_bk = reinterpret_cast<uint8_t*>(p);
+    sm.table = nullptr;
+    sm.stage = nullptr;
+    sm.wst = nullptr;
+    sm.queue = nullptr;
+    sm.ring = nullptr;
+    sm.ring_sp = nullptr;
+  }
+  __shared__ int64_t s_hub;
+  __shared__ unsigned long long s_pending;
+  __shared__ int s_flush, s_cat, s_cur, s_next;
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (LUT)
+    for (int k = tid; k < nb * nb * nb; k += kPThreads)
+      sm.lut[k] = (uint16_t)conf3_rank(k / (nb * nb), (k / nb) % nb, k % nb, nb);
+  for (int k = tid; k < a.nconf; k += kPThreads) sm.hist[k] = 0;
+  if (WEIGHTED) {
+    for (int k = tid; k < 2 * a.nconf; k += kPThreads) sm.whist[k] = 0;
+    for (int k = tid; k < 3 * a.nconf; k += kPThreads) sm.hacc[k] = 0;
+  }
+  for (int b = tid; b <= nb; b += kPThreads) s_e2[b] = a.e2g[b];
+  for (int k = tid; BIN != kBinLinear && k < a.bk_n; k += kPThreads) {
+    const int64_t x = (int64_t)k << a.bk_shift;
+    int b = 0;
+    while (b + 1 < nb && a.e2g[b + 1] <= x) ++b;
+    s_bk[k] = (BIN == kBinTable && x < a.e2g[0]) ? (uint8_t)0xFF : (uint8_t)b;
+  }
+  if (tid == 0) {
+    s_pending = 0;
+    s_cur = BATCH ? -1 : 0;
+  }
+  __syncthreads();
+  const int64_t e2lo = s_e2[0], e2hi = s_e2[nb];
+  const uint8_t* bk = (BIN != kBinLinear && a.bk_n) ? s_bk : nullptr;
+  Cat c = a.one;
+  int cur = BATCH ? -1 : 0;
+
+  auto flush = [&]() {
+    if (cur < 0) return;
+    for (int k = tid; k < a.nconf; k += kPThreads) {
+      const unsigned v = sm.hist[k];
+      if (v) {
+        atomicAdd(c.counts + k, (unsigned long long)v);
+        sm.hist[k] = 0;
+      }
+      if (WEIGHTED) {
+        const unsigned long long lo = sm.whist[2 * k], hi = sm.whist[2 * k + 1];
+        if (lo | hi) {
+          atomic_add_i192(c.wacc + 3 * k, lo, hi);
+          sm.whist[2 * k] = sm.whist[2 * k + 1] = 0;
+        }
+      }
+    }
+  };
+  // the hub's 96-bit sums of W_j W_k, times W_i, into the CTA's 128-bit sums
+  auto fold_hub = [&](int64_t Wi) {
+    if constexpr (WEIGHTED) {
+      for (int k = tid; k < a.nconf; k += kPThreads) {
+        const uint32_t l = sm.hacc[3 * k], m = sm.hacc[3 * k + 1], h = sm.hacc[3 * k + 2];
+        if (!(l | m | h)) continue;
+        sm.hacc[3 * k] = sm.hacc[3 * k + 1] = sm.hacc[3 * k + 2] = 0u;
+        const unsigned long long ml = ((unsigned long long)m << 32) | l;
+        const unsigned long long uw = (unsigned long long)Wi;
+        const unsigned long long plo = ml * uw;
+        unsigned long long phi = __umul64hi(ml, uw) - (Wi < 0 ? ml : 0ull);
+        phi += (unsigned long long)((long long)(int32_t)h * Wi);
+        const unsigned long long olo = sm.whist[2 * k];
+        const unsigned long long nlo = olo + plo;
+        sm.whist[2 * k] = nlo;
+        sm.whist[2 * k + 1] += phi + ((nlo < olo) ? 1ull : 0ull);
+      }
+    }
+  };
+  // Pairs (ra, rb), ra < rb, of the staged row: warps take rows ra from a
+  // shared counter (long rows first), lanes take rb. A staged entry's fourth
+  // word is the hub edge's bin, premultiplied by nb for the configuration
+  // table. EXACT: every bin edge E_b^2 is a multiple of the bucket width, so
+  // a bucket holds one bin (or 0xFF below E_0) and the bucket lookup is the
+  // whole test; otherwise the squared distance is range-tested and the
+  // bucket's bin is finished by one comparison with the next edge.
+  const uint32_t s_hist = (uint32_t)__cvta_generic_to_shared(sm.hist);
+  const uint32_t s_hacc = WEIGHTED ? (uint32_t)__cvta_generic_to_shared(sm.hacc) : 0u;
+  const unsigned long long span = (unsigned long long)(e2hi - e2lo);
+  // a staged entry's x displacement and tag (see the staging loop)
+  auto ent_x = [](const int4& e) -> int {
+    return WEIGHTED ? (int)((uint32_t)e.x << 11) >> 11 : e.x;
+  };
+  auto ent_tag = [](const int4& e) -> int {
+    return WEIGHTED ? (int)((uint32_t)e.x >> 21) : e.w;
+  };
+  auto pair = [&](int xa, const int4& Da, int taga, const int4& Db, int abase, int32_t Wa) {
+    const int x = ent_x(Db) - xa, y = Db.y - Da.y, z = Db.z - Da.z;
+    const unsigned long long D2 =
+        (unsigned long long)((long long)x * x + (long long)y * y + (long long)z * z);
+    int bjk;
+    if constexpr (BIN == kBinLinear) {
+      // q < (m nb)^2 <= 2^18 is exact in FP32; for q in [(m b)^2, (m (b+1))^2)
+      // sqrt(q) / m lies in [b, b + 1 - 1 / (2 m^2 (b + 1))], and the
+      // approximate square root (relative error below 2^-22 with the
+      // multiply) raised by 2^-20 lands strictly inside [b, b + 1) when
+      // m nb <= 512, so truncation gives b exactly
+      const unsigned long long q = D2 >> a.bk_shift;
+      if (q >= (unsigned long long)a.bk_n) return;
+      float r;
+      asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"((float)(uint32_t)q));
+      bjk = (int)(r * a.lin_c);
+    } else if constexpr (BIN == kBinTable) {
+      const unsigned long long q = D2 >> a.bk_shift;
+      if (q >= (unsigned long long)a.bk_n) return;
+      bjk = bk[q];
+      if (bjk == 0xFF) return;
+    } else {
+      if (D2 - (unsigned long long)e2lo >= span) return;
+      if (bk) {
+        const int b0 = bk[D2 >> a.bk_shift];
+        bjk = b0 + ((long long)D2 >= s_e2[b0 + 1] ? 1 : 0);
+      } else {
+        int lo = 0, hi = nb;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_e2[mid] <= (long long)D2) lo = mid;
+          else hi = mid;
+        }
+        bjk = lo;
+      }
+    }
+    const int tagb = ent_tag(Db);
+    const int cf = LUT ? (int)sm.lut[abase + tagb + bjk] : conf3_rank(taga, tagb, bjk, nb);
+    record_if<WM>(s_hist, s_hacc, cf, true, Wa, WEIGHTED ? Db.w : 0);
+  };
+  auto pairs = [&](const int4* S, int d) {
+    for (;;) {
+      int ra = 0;
+      if (lane == 0) ra = atomicAdd(&s_next, 1);
+      ra = __shfl_sync(0xffffffffu, ra, 0);
+      if (ra >= d - 1) break;
+      const int4 Da = S[ra];
+      const int xa = ent_x(Da), taga = ent_tag(Da);
+      const int32_t Wa = WEIGHTED ? Da.w : 0;
+      const int abase = LUT ? taga * nb : 0;  // b_ij nb^2
+      int rb = ra + 1 + lane;
+      for (; rb + 32 < d; rb += 64) {
+        const int4 D0 = S[rb], D1 = S[rb + 32];
+        pair(xa, Da, taga, D0, abase, Wa);
+        pair(xa, Da, taga, D1, abase, Wa);
+      }
+      if (rb < d) pair(xa, Da, taga, S[rb], abase, Wa);
+    }
+  };
+
+  for (;;) {
+    if (tid == 0) {
+      const int64_t q = (int64_t)atomicAdd(a.hub_counter, 1ull);
+      int k = 0;
+      int64_t hub;
+      bool valid;
+      if (BATCH) {
+        valid = q < a.base[a.ncats];
+        if (valid) {
+          int lo = 0, hi = a.ncats;  // largest k with base[k] <= q
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.base[mid] <= q) lo = mid;
+            else hi = mid;
+          }
+          k = lo;
+        }
+        hub = valid ? q - a.base[k] : 0;
+      } else {
+        hub = a.one.hub_begin + q;
+        valid = hub < a.one.hub_end;
+      }
+      s_hub = valid ? hub : -1;
+      s_cat = k;
+      s_flush = 0;
+      s_next = 0;
+      if (valid) {
+        const int32_t* dg = BATCH ? a.cats[k].deg : a.one.deg;
+        const unsigned long long d = (unsigned long long)dg[hub];
+        const unsigned long long need = d * (d - (d > 0)) / 2;  // triangles at i <= C(d,2)
+        if (k != s_cur || s_pending + need > 0xFFFFFFFFull) {
+          s_flush = 1;
+          s_pending = need;
+          s_cur = k;
+        } else {
+          s_pending += need;
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t i = s_hub;
+    if (i < 0) break;
+    if (s_flush) {
+      flush();
+      __syncthreads();
+    }
+    if (BATCH && s_cat != cur) {
+      cur = s_cat;
+      c = a.cats[cur];
+    }
+    const int d = c.deg[i];
+    if (d < 2) {
+      __syncthreads();
+      continue;
+    }
+    const uint32_t* row = row_at(c.adj, c.ptr, i, c.adj_off, c.split, c.adj_off2);
+    const int4 P = c.xyzp[i];
+    const bool big = d > a.cap;
+    int4* gS = reinterpret_cast<int4*>(a.gscratch + (size_t)blockIdx.x * a.gstride);
+    int4* S = big ? gS : s_stage;
+    for (int t = tid; t < d; t += kPThreads) {
+      const uint32_t w = row[t];
+      const uint32_t k = edge_id(w);
+      const int4 Q = c.xyzp[k];
+      const int dx = (int)min_image((int64_t)Q.x - P.x, c.box);
+      const int tag = (int)edge_bin(w) * (LUT ? nb : 1);
+      // weighted: the tag rides in bits 21..30 above the 21-bit x
+      // displacement (|dx| < 2^19), the fourth word is W_k
+      S[t] = make_int4(WEIGHTED ? (int)(((uint32_t)dx & 0x1FFFFFu) | ((uint32_t)tag << 21)) : dx,
+                       (int)min_image((int64_t)Q.y - P.y, c.box),
+                       (int)min_image((int64_t)Q.z - P.z, c.box),
+                       WEIGHTED ? (int)c.W[k] : tag);
+    }
+    __syncthreads();
+    if (big) pairs(gS, d);
+    else pairs(s_stage, d);
+    __syncthreads();
+    fold_hub(WEIGHTED ? (int64_t)c.W[i] : 0);
+  }
+  __syncthreads();
+  flush();
+}
+
+template <bool BATCH>
+void (*pick_count3p(int wm, bool nonneg, bool lut, int bin))(PArgs) {
+#define GS_P2(W, L)                                                        \
+  (bin == kBinLinear  ? k_count3p<W, BATCH, L, kBinLinear>                 \
+   : bin == kBinTable ? k_count3p<W, BATCH, L, kBinTable>                  \
+                      : k_count3p<W, BATCH, L, kBinSearch>)
+#define GS_P(W) (lut ? GS_P2(W, true) : GS_P2(W, false))
+  if (wm == kNone) return GS_P(kNone);
+  return nonneg ? GS_P(kExactPos) : GS_P(kExact);
+#undef GS_P
+#undef GS_P2
+}
+
 // Shared-memory layout of k_count3: the direct-address table takes what the
 // staging buffer, configuration table and histograms leave.
 struct Count3Launch {
@@ -814,6 +1194,90 @@ Count3Launch count3_launch(int nb, int nconf, int wmode, bool use_lut, bool comp
   L.stage_words = (int)stage_words;
   L.smem = (size_t)L.span_cap + fixed + hist;
   return L;
+}
+
+// Launch plan of the pair kernel: shared-memory layout sized for two CTAs
+// per SM when it fits (one otherwise), squared-distance buckets, and the
+// global staging for hubs above the shared capacity.
+struct PairLaunch {
+  size_t smem = 0;
+  int cap = 0;
+  int per_sm = 0;
+  bool lut = false;
+  int bin = kBinSearch;
+  int bk_shift = 0, bk_n = 0;  // kBinLinear: q = D2 >> bk_shift, edges iff q < bk_n
+  float lin_c = 0.0f;
+};
+
+PairLaunch pair_launch(int nb, int nconf, bool weighted, bool use_lut,
+                       const std::vector<int64_t>& edges) {
+  PairLaunch L;
+  int dev = 0, optin = 0, per_sm_bytes = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  auto pad16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  // Exact buckets when every squared edge is a multiple of a power of two
+  // 2^sx that leaves at most kPBucketExactMax buckets below E_nb^2 (edges
+  // on a coarse lattice, e.g. E_b = 2048 b); otherwise buckets no wider
+  // than the narrowest bin in squared distance, finished by a comparison.
+  const int64_t top = edges[nb] * edges[nb];
+  int sx = 62;
+  for (int b = 0; b <= nb; ++b) {
+    const int64_t e2 = edges[b] * edges[b];
+    if (e2) sx = std::min(sx, __builtin_ctzll((unsigned long long)e2));
+  }
+  const int64_t nbx = ((top - 1) >> sx) + 1;
+  // linear bins from zero: E_b = b E_1 with E_1 = m 2^t, m odd, m nb <= 512
+  bool linear = edges[0] == 0 && edges[1] > 0;
+  for (int b = 2; b <= nb && linear; ++b) linear = edges[b] == b * edges[1];
+  int t = 0;
+  int64_t m = linear ? edges[1] : 0;
+  while (linear && m % 2 == 0) {
+    m /= 2;
+    ++t;
+  }
+  if (linear && m * nb <= 512) {
+    L.bin = kBinLinear;
+    L.bk_shift = 2 * t;
+    L.bk_n = (int)(m * m * nb * nb);  // (E_nb / 2^t)^2
+    L.lin_c = (float)((1.0 / (double)m) * (1.0 + std::ldexp(1.0, -20)));
+  } else if (nbx <= kPBucketExactMax && nb < 255) {
+    L.bin = kBinTable;
+    L.bk_shift = sx;
+    L.bk_n = (int)nbx;
+  } else {
+    int64_t gap = INT64_MAX;
+    for (int b = 0; b < nb; ++b)
+      gap = std::min(gap, edges[b + 1] * edges[b + 1] - edges[b] * edges[b]);
+    int sh = 0;
+    while (sh < 62 && (int64_t(1) << (sh + 1)) <= gap) ++sh;
+    const int64_t nbk = ((top - 1) >> sh) + 1;
+    if (gap >= 1 && nbk <= kPBucketMax) {
+      L.bk_shift = sh;
+      L.bk_n = (int)nbk;
+    }
+  }
+  const size_t nb3 = (size_t)nb * nb * nb;
+  L.lut = use_lut && nb3 <= (size_t)kLutMax;
+  const size_t fixed = pad16((size_t)(nb + 1) * 8) + (L.lut ? pad16(nb3 * 2) : 0) +
+                       pad16((size_t)nconf * 4) + (weighted ? (size_t)nconf * 28 : 0) +
+                       (L.bin == kBinLinear ? 0 : pad16((size_t)L.bk_n));
+  const size_t per = 16;  // one int4 per staged neighbour
+  const size_t static_bytes = 256;  // the kernel's own __shared__ variables and slack
+  for (int ctas = 2; ctas >= 1; --ctas) {
+    const size_t budget =
+        std::min((size_t)optin, (size_t)per_sm_bytes / ctas - 1024) - static_bytes;
+    if (budget <= fixed) continue;
+    int cap = (int)std::min<size_t>(4096, (budget - fixed) / per) & ~31;
+    if (cap < 256 && ctas == 2) continue;
+    if (cap < 32) continue;
+    L.cap = cap;
+    L.smem = (size_t)cap * per + fixed;
+    L.per_sm = ctas;
+    return L;
+  }
+  return L;  // cap 0: the configuration tables leave no room (walk kernel instead)
 }
 
 }  // namespace
@@ -911,6 +1375,62 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   }
 
   const bool use_lut = !equi && !(o.variant & 4);
+  a.one.xyzp = g.d_xyzp;
+  a.one.box = g.box_u;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  KernelTimer timer(o.kernel_ms);
+  int st = GS_OK;
+  // The pair kernel is the default. Launch bits of the walk's own paths
+  // (1, 2, 8, 16, 32, 64, 512), the equilateral configurations and rows of
+  // more than 65,535 neighbours (whose triangles could overflow the 32-bit
+  // shared counters within one hub) take the merge-walk kernel.
+  const bool pair_ok = !equi && (o.variant & ~4) == 0 && g.max_deg <= kMaxSmemHistDeg;
+  const PairLaunch PL = pair_ok ? pair_launch(g.nb, nconf, wm != kNone, use_lut, g.edges)
+                                : PairLaunch{};
+  if (PL.cap > 0) {
+    PArgs pa;
+    pa.one = a.one;
+    pa.cats = nullptr;
+    pa.base = nullptr;
+    pa.ncats = 0;
+    pa.nb = g.nb;
+    pa.nconf = nconf;
+    pa.cap = PL.cap;
+    pa.use_lut = PL.lut ? 1 : 0;
+    pa.bk_shift = PL.bk_shift;
+    pa.bk_n = PL.bk_n;
+    pa.e2g = g.d_edges2;
+    pa.hub_counter = a.hub_counter;
+    pa.lin_c = PL.lin_c;
+    void (*kern)(PArgs) =
+        pick_count3p<false>(wm, fw && fw->nonneg, PL.lut, PL.bin);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL.smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, PL.smem);
+    const int grid = std::max(1, per_sm) * sms;
+    pa.gscratch = nullptr;
+    pa.gstride = 0;
+    if (g.max_deg > PL.cap) {
+      pa.gstride = ((size_t)g.max_deg * 16 + 255) & ~(size_t)255;
+      pa.gscratch = sc.alloc<unsigned char>(pa.gstride * grid);
+      if (!pa.gscratch) return GS_ENOMEM;
+    }
+    timer.start(s);
+    st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+      pa.one.adj = v.adj;
+      pa.one.adj_off = v.off1;
+      pa.one.split = v.split;
+      pa.one.adj_off2 = v.off2;
+      pa.one.hub_begin = v.h0;
+      pa.one.hub_end = v.h1;
+      cudaMemsetAsync(pa.hub_counter, 0, sizeof(unsigned long long), s);
+      { kern<<<grid, kPThreads, PL.smem, s>>>(pa); note_launch(); }
+      return cuda_status(cudaGetLastError());
+    });
+    timer.stop(s);
+  } else {
   const Count3Launch L =
       count3_launch(g.nb, nconf, wm, use_lut, (o.variant & 32) != 0, (o.variant & 64) != 0,
                     g.max_deg);
@@ -927,14 +1447,11 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   kern = equi ? pick_equi3(wm, fw && fw->nonneg, smem_hist)
               : pick_count3<false>(wm, fw && fw->nonneg, smem_hist, L.lut);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   const int grid = std::max(1, per_sm) * sms;
-  KernelTimer timer(o.kernel_ms);
   timer.start(s);
-  int st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+  st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
     a.one.adj = v.adj;
     a.one.adj_off = v.off1;
     a.one.split = v.split;
@@ -946,6 +1463,7 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
     return cuda_status(cudaGetLastError());
   });
   timer.stop(s);
+  }
   if (st) return st;
   cudaError_t e;
   if (d_wsum) {
@@ -989,6 +1507,8 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
     c.wacc = wm == kExact ? wacc + 3 * (size_t)nconf * k : nullptr;
     c.hub_begin = 0;
     c.hub_end = g.n;
+    c.xyzp = g.d_xyzp;
+    c.box = g.box_u;
     base[k + 1] = base[k] + g.n;
     cudaMemsetAsync(d_counts[k], 0, sizeof(uint64_t) * nconf, s);
   }
@@ -1014,6 +1534,52 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
   int max_deg = 0;
   for (int k = 0; k < ng; ++k) max_deg = std::max(max_deg, gr[k]->max_deg);
+  bool nonneg = true;
+  for (int k = 0; k < ng && fws; ++k) nonneg = nonneg && fws[k].nonneg;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  KernelTimer timer(o.kernel_ms);
+  // the pair kernel when the catalogues share their bin edges (one bucket
+  // table serves them all), else the merge-walk kernel
+  bool same_edges = true;
+  for (int k = 1; k < ng; ++k) same_edges = same_edges && gr[k]->edges == gr[0]->edges;
+  const bool pair_ok = same_edges && (o.variant & ~4) == 0 && max_deg <= kMaxSmemHistDeg;
+  const PairLaunch PL = pair_ok ? pair_launch(nb, nconf, wm != kNone, !(o.variant & 4),
+                                              gr[0]->edges)
+                                : PairLaunch{};
+  if (PL.cap > 0) {
+    PArgs pa;
+    pa.one = cats[0];
+    pa.cats = d_cats;
+    pa.base = d_base;
+    pa.ncats = ng;
+    pa.nb = nb;
+    pa.nconf = nconf;
+    pa.cap = PL.cap;
+    pa.use_lut = PL.lut ? 1 : 0;
+    pa.bk_shift = PL.bk_shift;
+    pa.bk_n = PL.bk_n;
+    pa.e2g = gr[0]->d_edges2;
+    pa.hub_counter = a.hub_counter;
+    pa.lin_c = PL.lin_c;
+    void (*kern)(PArgs) =
+        pick_count3p<true>(wm, nonneg, PL.lut, PL.bin);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL.smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, PL.smem);
+    const int grid = std::max(1, per_sm) * sms;
+    pa.gscratch = nullptr;
+    pa.gstride = 0;
+    if (max_deg > PL.cap) {
+      pa.gstride = ((size_t)max_deg * 16 + 255) & ~(size_t)255;
+      pa.gscratch = sc.alloc<unsigned char>(pa.gstride * grid);
+      if (!pa.gscratch) return GS_ENOMEM;
+    }
+    timer.start(s);
+    if (base[ng] > 0) { kern<<<grid, kPThreads, PL.smem, s>>>(pa); note_launch(); }
+    timer.stop(s);
+  } else {
   const Count3Launch L =
       count3_launch(nb, nconf, wm, !(o.variant & 4), (o.variant & 32) != 0, (o.variant & 64) != 0,
                     max_deg);
@@ -1027,18 +1593,14 @@ int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint6
   const bool smem_hist = L.smem_hist;
   const size_t smem = L.smem;
   void (*kern)(Args);
-  bool nonneg = true;
-  for (int k = 0; k < ng && fws; ++k) nonneg = nonneg && fws[k].nonneg;
   kern = pick_count3<true>(wm, nonneg, smem_hist, L.lut);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  KernelTimer timer(o.kernel_ms);
   timer.start(s);
   if (base[ng] > 0) { kern<<<std::max(1, per_sm) * sms, kThreads, smem, s>>>(a); note_launch(); }
   timer.stop(s);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   for (int k = 0; k < ng; ++k) {
@@ -1162,6 +1724,8 @@ extern "C" int gs_count_3pcf_noalloc(const gs_graph* G, uint64_t* counts,
     a.one.wacc = nullptr;
     a.one.hub_begin = 0;
     a.one.hub_end = g.n;
+    a.one.xyzp = g.d_xyzp;
+    a.one.box = g.box_u;
     a.cats = nullptr;
     a.base = nullptr;
     a.ncats = 0;
@@ -1248,6 +1812,8 @@ extern "C" int gs_plan_3pcf_batch(const gs_graph* const* graphs, int32_t n_graph
     c.wacc = nullptr;
     c.hub_begin = 0;
     c.hub_end = g.n;
+    c.xyzp = g.d_xyzp;
+    c.box = g.box_u;
     base[k + 1] = base[k] + g.n;
   }
   cudaError_t e = cudaMalloc(&P->d_cats, sizeof(Cat) * n_graphs);
@@ -1370,9 +1936,11 @@ extern "C" int gs_tune_3pcf(const gs_graph* G, const float* w, const gs_options*
   Opts o = read_opts(options);
   const int nconf = (int)num_conf3(g.nb);
   const int wmode = w ? kExact : kNone;
-  // staged vs global hub rows, table vs computed configuration ranks,
-  // (weighted) per-warp hit compaction, and the spoke-row prefetch ring
-  static const int kCandidates[8] = {0, 2, 4, 6, 32, 34, 64, 96};
+  // the pair kernel (table or computed configuration ranks) and the
+  // merge-walk kernel (512) with staged or global hub rows (2), table or
+  // computed ranks (4), (weighted) per-warp hit compaction (32) and the
+  // spoke-row prefetch ring (64)
+  static const int kCandidates[10] = {0, 4, 512, 514, 516, 518, 544, 546, 576, 608};
   int best = 0;
   double best_ms = 1e300;
   int st = GS_OK;

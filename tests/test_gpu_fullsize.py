@@ -98,7 +98,8 @@ def test_fullsize_open_box_subbox(gs, windows):
     (X, box_u, edges, _), d = expected("c4sub")
     Xd = torch.from_numpy(X).cuda()
     g = gs.gs_build_graph(Xd, 0, edges, force_windows=windows)
-    assert gs.gs_graph_info(g)["windows"] == max(1, windows)
+    nw = gs.gs_graph_info(g)["windows"]
+    assert nw == 1 if windows == 0 else nw >= 2
     c = gs.gs_count_3pcf(g, like=Xd).cpu().numpy()
     assert d["counts"].sum() > 1e9
     assert np.array_equal(c, d["counts"])

@@ -172,13 +172,16 @@ def test_3pcf_clustered_weighted(gs, torch_mod, periodic, seed):
     assert np.array_equal(gw, rw)
     # unweighted call on the same graph agrees with the weighted call's counts
     assert np.array_equal(run3(gs, torch_mod, X, bu, edges), rc)
-    # every kernel path gives the same answer: hash path in 64-word segments
-    # (variant 1) and the table path reading hub rows from global (variant 2)
+    # every kernel gives the same answer: the default pair kernel (0, and 4
+    # with computed configuration ranks) and the merge-walk kernel (512 and
+    # every bit of its own paths: hash path in 64-word segments (1), hub rows
+    # from global memory (2), a 2 KB table (8), compaction (32), the prefetch
+    # ring (64))
     g = gs.gs_build_graph(X, bu, edges)
     ex_c, ex_w = gs.gs_count_3pcf(g, w)
     assert np.array_equal(ex_c, rc)
     assert np.array_equal(ex_w, rw)
-    for variant in (1, 2, 4, 6, 8, 10, 32, 34, 36, 40, 64, 68, 72, 96):
+    for variant in (4, 512, 516, 1, 2, 6, 8, 10, 32, 34, 36, 40, 64, 68, 72, 96):
         vc, vw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(vc, rc), variant
         assert np.array_equal(vw, rw), variant
@@ -201,7 +204,7 @@ def test_3pcf_signed_weights(gs, torch_mod):
     rc, rw = oracle.Graph(X, box_u, edges).count_3pcf(w)
     assert np.any(rw < 0) and np.any(rw > 0)
     g = gs.gs_build_graph(X, box_u, edges)
-    for variant in (0, 1, 4, 32, 64):
+    for variant in (0, 4, 512, 1, 32, 64):
         gc, gw = gs.gs_count_3pcf(g, w, variant=variant)
         assert np.array_equal(gc, rc), variant
         assert np.array_equal(gw, rw), variant
@@ -239,6 +242,29 @@ def test_weighted_sum_rounds_to_nearest_at_a_tie(gs, torch_mod):
         assert e.sum() == 1 and np.array_equal(e, re) and np.array_equal(o, ro)
         assert we[e.argmax()] == sign * float(exact)
         assert np.array_equal(we, rwe) and np.array_equal(wo, rwo)
+
+
+@pytest.mark.parametrize("rmin,rmax,nb", [(0.0, 12.0, 8), (1.0, 9.0, 8), (0.0, 10.3, 7)])
+def test_3pcf_pair_kernel_binning_modes(gs, torch_mod, rmin, rmax, nb):
+    """The pair kernel bins a pair's squared distance three ways, chosen by
+    the bin edges: linear bins from zero (E_b = b m 2^t) by a square root,
+    edges whose squares share a power-of-two factor (here E_b = 1024 (b + 1),
+    with r_min > 0) by one table lookup that also rejects pairs closer than
+    E_0, and any other edges by a range test and a comparison. Each against
+    the oracle and the merge-walk kernel, weighted and unweighted."""
+    L = 100.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(15_000, L, seed=int(10 * rmax) + nb, sigma=1.5)
+    X = oracle.quantize(pos, box_u, True)
+    w = catalogs.uniform_weights(len(X), seed=nb)
+    edges = catalogs.bin_edges_u(rmin, rmax, nb)
+    rc, rw = oracle.Graph(X, box_u, edges).count_3pcf(w)
+    assert rc.sum() > 100_000
+    g = gs.gs_build_graph(X, box_u, edges)
+    for variant in (0, 4, 512):
+        c, ws = gs.gs_count_3pcf(g, w, variant=variant)
+        assert np.array_equal(c, rc) and np.array_equal(ws, rw), variant
+        assert np.array_equal(gs.gs_count_3pcf(g, variant=variant), rc), variant
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
