@@ -83,6 +83,12 @@ def _load():
     lib.or_disconnected.restype = ci
     lib.or_connected_4pcf.argtypes = [P, P, P, P, P, P, P, P, P, ci]
     lib.or_connected_4pcf.restype = ci
+    lib.or_count_4pcf_pix.argtypes = [P, P, P, P, P, P, ci]
+    lib.or_count_4pcf_pix.restype = ci
+    lib.or_direction_pixels.argtypes = [P, i64, P]
+    lib.or_direction_pixels.restype = None
+    lib.or_pixel_volumes.argtypes = [P, i64, P]
+    lib.or_pixel_volumes.restype = None
     lib.or_exact_to_double.argtypes = [P, ci]
     lib.or_exact_to_double.restype = ctypes.c_double
     _lib = lib
@@ -117,6 +123,23 @@ def exact_to_double(value: int, scale: int) -> float:
     u = v & ((1 << 256) - 1)
     words = np.array([(u >> (64 * k)) & ((1 << 64) - 1) for k in range(4)], dtype=np.uint64)
     return float(_load().or_exact_to_double(_ptr(words), int(scale)))
+
+
+def direction_pixels(d) -> np.ndarray:
+    """Pixel (0..255) of integer direction vectors d [n][3]: 16 equal-width
+    bands in z = cos(theta) times 16 equal sectors in phi, decided exactly."""
+    d = np.ascontiguousarray(d, dtype=np.int64).reshape(-1, 3)
+    out = np.empty(d.shape[0], dtype=np.uint8)
+    _load().or_direction_pixels(_ptr(d), d.shape[0], _ptr(out))
+    return out
+
+
+def pixel_volumes(p) -> np.ndarray:
+    """(u1 x u2) . u3 of the pixel centres of pixel triples p [n][3] (FP64)."""
+    p = np.ascontiguousarray(p, dtype=np.int32).reshape(-1, 3)
+    out = np.empty(p.shape[0], dtype=np.float64)
+    _load().or_pixel_volumes(_ptr(p), p.shape[0], _ptr(out))
+    return out
 
 
 def num_configs(npoint: int, nb: int) -> int:
@@ -172,16 +195,18 @@ class Graph:
             raise ValueError(f"oracle 3pCF failed ({st})")
         return (counts, wsum) if w is not None else counts
 
-    def count_4pcf(self, w=None):
-        """Returns (even u64, odd i64) or, with weights, (even, odd, weven, wodd)."""
+    def count_4pcf(self, w=None, pixel: bool = False):
+        """Returns (even u64, odd i64) or, with weights, (even, odd, weven, wodd).
+        pixel=True: odd channel from pixelised spoke directions (see
+        direction_pixels), degenerate tetrahedra (|V| < 1e-9) excluded."""
         nc = num_configs(4, self.nb)
         even = np.zeros(nc, dtype=np.uint64)
         odd = np.zeros(nc, dtype=np.int64)
         we = np.zeros(nc, dtype=np.float64) if w is not None else None
         wo = np.zeros(nc, dtype=np.float64) if w is not None else None
         wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
-        st = _load().or_count_4pcf(self._h, _ptr(wa), _ptr(even), _ptr(odd), _ptr(we), _ptr(wo),
-                                   self.nthreads)
+        fn = _load().or_count_4pcf_pix if pixel else _load().or_count_4pcf
+        st = fn(self._h, _ptr(wa), _ptr(even), _ptr(odd), _ptr(we), _ptr(wo), self.nthreads)
         if st != 0:
             raise ValueError(f"oracle 4pCF failed ({st})")
         return (even, odd, we, wo) if w is not None else (even, odd)

@@ -452,6 +452,77 @@ struct Conf4 {
   }
 };
 
+// ----------------------------------------------------------------------------
+// Direction pixels for the pixelised parity channel (Sec. 3.2: each spoke's
+// direction is quantised to a pixel on the unit sphere, one byte per edge;
+// tetrahedra whose pixel volume is below 1e-9 in magnitude are degenerate).
+// The paper does not fix the pixel scheme; the reading taken here is 256
+// equal-area pixels: 16 bands of equal width in z = cos(theta) times 16
+// sectors of equal width in the azimuth phi, pixel = 16 * band + sector.
+// Band and sector of an integer direction are decided exactly in integers:
+//   band   = number of k in 1..15 with z / |d| >= -1 + k / 8;
+//   sector = floor(phi / (pi / 8)), phi = atan2(y, x) in [0, 2 pi), and
+//            sector 0 for a direction along the z axis.
+// The pixel centre is z_c = -1 + (band + 1/2) / 8, phi_c = (sector + 1/2) pi / 8.
+
+// Whether z / |d| >= s / 8 for s in -7..7, with n2 = |d|^2 (exact).
+bool z_at_least(int64_t z, int64_t n2, int s) {
+  const int64_t lhs = 64 * z * z, rhs = (int64_t)s * s * n2;
+  if (s <= 0) return z >= 0 || lhs <= rhs;
+  return z > 0 && lhs >= rhs;
+}
+
+int direction_pixel(int64_t x, int64_t y, int64_t z) {
+  const int64_t n2 = x * x + y * y + z * z;
+  int band = 0;
+  for (int k = 1; k <= 15; ++k)
+    if (z_at_least(z, n2, k - 8)) ++band;
+  int sector = 0;
+  if (x != 0 || y != 0) {
+    // rotate by a multiple of pi/2 into a > 0, b >= 0 (theta in [0, pi/2))
+    int quadrant;
+    int64_t a, b;
+    if (x > 0 && y >= 0) { quadrant = 0; a = x; b = y; }
+    else if (x <= 0 && y > 0) { quadrant = 1; a = y; b = -x; }
+    else if (x < 0 && y <= 0) { quadrant = 2; a = -x; b = -y; }
+    else { quadrant = 3; a = -y; b = x; }
+    // theta >= pi/8  <=>  b >= (sqrt2 - 1) a  <=>  (a + b)^2 >= 2 a^2
+    // theta >= pi/4  <=>  b >= a
+    // theta >= 3pi/8 <=>  b >= (sqrt2 + 1) a  <=>  b > a and (b - a)^2 >= 2 a^2
+    int sub = 0;
+    if ((a + b) * (a + b) >= 2 * a * a) ++sub;
+    if (b >= a) ++sub;
+    if (b > a && (b - a) * (b - a) >= 2 * a * a) ++sub;
+    sector = 4 * quadrant + sub;
+  }
+  return 16 * band + sector;
+}
+
+void pixel_centre(int p, double u[3]) {
+  const int band = p / 16, sector = p % 16;
+  const double zc = -1.0 + (band + 0.5) / 8.0;
+  const double phi = (sector + 0.5) * M_PI / 8.0;
+  const double rho = std::sqrt(1.0 - zc * zc);
+  u[0] = rho * std::cos(phi);
+  u[1] = rho * std::sin(phi);
+  u[2] = zc;
+}
+
+// (u1 x u2) . u3 of three pixel centres, FP64, left to right (no contraction:
+// the file is compiled with -ffp-contract=off).
+double pixel_volume(int p1, int p2, int p3) {
+  double a[3], b[3], c[3];
+  pixel_centre(p1, a);
+  pixel_centre(p2, b);
+  pixel_centre(p3, c);
+  const double cx = a[1] * b[2] - a[2] * b[1];
+  const double cy = a[2] * b[0] - a[0] * b[2];
+  const double cz = a[0] * b[1] - a[1] * b[0];
+  return cx * c[0] + cy * c[1] + cz * c[2];
+}
+
+constexpr double kDegenerateVolume = 1e-9;
+
 Conf4* conf4_cached(int nb) {
   static std::map<int, Conf4*> cache;
   static std::mutex mu;
@@ -602,8 +673,13 @@ int or_count_3pcf(void* gp, const float* w, uint64_t* counts, double* wsum, int6
 
 // Sec. 2.2, Eq. (threeway), Sec. 3.2: tetrahedra i < j1 < j2 < j3 found at
 // hub i; even/odd channels. Any output pointer may be NULL.
-int or_count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, double* weven,
-                  double* wodd, int nthreads) {
+// pixel != 0: the odd channel takes the sign of the pixel volume of the
+// hub's three spokes (the hub has the smallest index, j1 < j2 < j3), times
+// the parity of the relabelling onto the orbit representative, and nothing
+// when that volume is below 1e-9 in magnitude (the pixelised reading of
+// Sec. 3.2); otherwise the exact integer V in the representative's order.
+static int count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, double* weven,
+                      double* wodd, int nthreads, int pixel) {
   Graph& g = *(Graph*)gp;
   Conf4* conf = conf4_cached(g.nb);
   const size_t nconf = conf->reps.size();
@@ -651,13 +727,27 @@ int or_count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, double
               // vertices in the order that maps the tuple onto the representative
               const int64_t v[4] = {i, j1, j2, j3};
               const Perm4& pi = conf->perms[conf->perm[raw]];
-              int64_t d[3][3];
-              for (int k = 1; k <= 3; ++k) displacement(g, v[pi.p[0]], v[pi.p[k]], d[k - 1]);
-              const i128 V = (i128)d[0][0] * ((i128)d[1][1] * d[2][2] - (i128)d[1][2] * d[2][1]) -
-                             (i128)d[0][1] * ((i128)d[1][0] * d[2][2] - (i128)d[1][2] * d[2][0]) +
-                             (i128)d[0][2] * ((i128)d[1][0] * d[2][1] - (i128)d[1][1] * d[2][0]);
-              if (V != 0) {
-                const int s = V > 0 ? 1 : -1;
+              int s = 0;
+              if (pixel) {
+                int px[3];
+                const int64_t u[3] = {j1, j2, j3};
+                for (int k = 0; k < 3; ++k) {
+                  int64_t d[3];
+                  displacement(g, i, u[k], d);
+                  px[k] = direction_pixel(d[0], d[1], d[2]);
+                }
+                const double Vp = pixel_volume(px[0], px[1], px[2]);
+                if (std::fabs(Vp) >= kDegenerateVolume) s = (Vp > 0 ? 1 : -1) * pi.sign;
+              } else {
+                int64_t d[3][3];
+                for (int k = 1; k <= 3; ++k) displacement(g, v[pi.p[0]], v[pi.p[k]], d[k - 1]);
+                const i128 V =
+                    (i128)d[0][0] * ((i128)d[1][1] * d[2][2] - (i128)d[1][2] * d[2][1]) -
+                    (i128)d[0][1] * ((i128)d[1][0] * d[2][2] - (i128)d[1][2] * d[2][0]) +
+                    (i128)d[0][2] * ((i128)d[1][0] * d[2][1] - (i128)d[1][1] * d[2][0]);
+                if (V != 0) s = V > 0 ? 1 : -1;
+              }
+              if (s != 0) {
                 ho[tid][o] += s;
                 if (w) hwo[tid][o].add(s > 0 ? prod : -prod);
               }
@@ -692,6 +782,28 @@ int or_count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, double
     if (wodd) wodd[c] = w ? ao.to_double(4 * fw.S) : (double)so;
   }
   return 0;
+}
+
+int or_count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, double* weven,
+                  double* wodd, int nthreads) {
+  return count_4pcf(gp, w, even, odd, weven, wodd, nthreads, 0);
+}
+
+// Sec. 3.2 with pixelised directions (the reading described at
+// direction_pixel): even channel as or_count_4pcf, odd channel from the
+// sign of the pixel volume, degenerate tetrahedra (|V| < 1e-9) excluded.
+int or_count_4pcf_pix(void* gp, const float* w, uint64_t* even, int64_t* odd, double* weven,
+                      double* wodd, int nthreads) {
+  return count_4pcf(gp, w, even, odd, weven, wodd, nthreads, 1);
+}
+
+// Test hooks: the pixel of integer directions (n of them, [n][3]) and the
+// pixel volume of pixel triples ([n][3]).
+void or_direction_pixels(const int64_t* d, int64_t n, uint8_t* pix) {
+  for (int64_t k = 0; k < n; ++k) pix[k] = (uint8_t)direction_pixel(d[3 * k], d[3 * k + 1], d[3 * k + 2]);
+}
+void or_pixel_volumes(const int32_t* p, int64_t n, double* v) {
+  for (int64_t k = 0; k < n; ++k) v[k] = pixel_volume(p[3 * k], p[3 * k + 1], p[3 * k + 2]);
 }
 
 // Sec. 3.3: pair histogram over unordered edges; weighted sums exact.

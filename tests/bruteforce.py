@@ -8,6 +8,7 @@ exact Python-integer determinants for the parity volume.
 """
 from __future__ import annotations
 
+import functools
 import itertools
 from fractions import Fraction
 
@@ -175,3 +176,92 @@ def rows(X, box_u, edges_u):
         j = np.nonzero(B[i] >= 0)[0]
         out.append((j.astype(np.int64), B[i, j].astype(np.int64)))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Pixelised directions (the reading of Sec. 3.2 used here: 256 equal-area
+# pixels, 16 bands of equal width in cos(theta) times 16 sectors of equal
+# width in phi), restated independently with high-precision arithmetic.
+
+
+@functools.lru_cache(maxsize=None)
+def direction_pixel(x: int, y: int, z: int) -> int:
+    """Band from cos(theta) = z/|d| (16 bands of width 1/8 on [-1, 1], a
+    value on a band edge belongs to the upper band), sector from
+    phi = atan2(y, x) in [0, 2 pi) (16 sectors of pi/8, an edge belongs to
+    the upper sector); sector 0 on the z axis. Computed with mpmath at 60
+    digits; the only directions exactly on an edge are z = 0 (band edge) and
+    the axes and diagonals of the x-y plane (sector edges), handled exactly."""
+    import mpmath
+    mpmath.mp.dps = 60
+    x, y, z = int(x), int(y), int(z)
+    if z == 0:
+        band = 8
+    else:
+        c = mpmath.mpf(z) / mpmath.sqrt(mpmath.mpf(x * x + y * y + z * z))
+        band = min(15, int(mpmath.floor((c + 1) * 8)))
+    if x == 0 and y == 0:
+        sector = 0
+    elif x == 0 or y == 0 or abs(x) == abs(y):
+        # exactly on a multiple of pi/4
+        eighth = {(1, 0): 0, (1, 1): 1, (0, 1): 2, (-1, 1): 3, (-1, 0): 4, (-1, -1): 5,
+                  (0, -1): 6, (1, -1): 7}
+        sgn = lambda v: (v > 0) - (v < 0)  # noqa: E731
+        sector = 2 * eighth[(sgn(x), sgn(y))]
+    else:
+        phi = mpmath.atan2(y, x)
+        if phi < 0:
+            phi += 2 * mpmath.pi
+        sector = int(mpmath.floor(phi / (mpmath.pi / 8)))
+    return 16 * band + sector
+
+
+def pixel_centre(p: int):
+    import math
+    band, sector = divmod(p, 16)
+    zc = -1.0 + (band + 0.5) / 8.0
+    phi = (sector + 0.5) * math.pi / 8.0
+    rho = math.sqrt(1.0 - zc * zc)
+    return (rho * math.cos(phi), rho * math.sin(phi), zc)
+
+
+def pixel_volume(p1: int, p2: int, p3: int) -> float:
+    a, b, c = pixel_centre(p1), pixel_centre(p2), pixel_centre(p3)
+    cx = a[1] * b[2] - a[2] * b[1]
+    cy = a[2] * b[0] - a[0] * b[2]
+    cz = a[0] * b[1] - a[1] * b[0]
+    return cx * c[0] + cy * c[1] + cz * c[2]
+
+
+def count4_pixel(X, box_u, edges_u):
+    """Even/odd 4-point counts with the odd sign from pixelised directions:
+    the tetrahedron's vertices in ascending index order (o, v1, v2, v3), the
+    spokes o -> vk, V = pixel volume of their pixels; odd += sign(V) times
+    the parity of a relabelling onto the orbit representative, when the orbit
+    is chiral and |V| >= 1e-9."""
+    import networkx as nx
+    nb = len(edges_u) - 1
+    B = bin_matrix(X, box_u, edges_u)
+    d = displacements(X, box_u)
+    conf = configs4(nb)
+    G = nx.Graph()
+    G.add_nodes_from(range(X.shape[0]))
+    ii, jj = np.nonzero(np.triu(B >= 0, 1))
+    G.add_edges_from(zip(ii.tolist(), jj.tolist()))
+    even = np.zeros(len(conf), dtype=np.uint64)
+    odd = np.zeros(len(conf), dtype=np.int64)
+    for cl in nx.enumerate_all_cliques(G):
+        if len(cl) < 4:
+            continue
+        if len(cl) > 4:
+            break
+        v = sorted(cl)
+        rep, p = canonical4(lambda a, b: int(B[v[a], v[b]]))
+        k, chiral = conf[rep]
+        even[k] += 1
+        if chiral:
+            pix = [direction_pixel(*(int(t) for t in d[v[0], v[m]])) for m in (1, 2, 3)]
+            V = pixel_volume(*pix)
+            if abs(V) >= 1e-9:
+                odd[k] += (1 if V > 0 else -1) * perm_sign(p)
+    return even, odd

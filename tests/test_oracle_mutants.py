@@ -16,11 +16,12 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "gs_oracle.cpp")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_rounding.py",
-        "tests/test_oracle_tooling.py", "tests/test_oracle_connected.py"]
+        "tests/test_oracle_tooling.py", "tests/test_oracle_connected.py",
+        "tests/test_oracle_pixel.py"]
 
 # (name, text in the oracle, replacement)
 MUTANTS = [
-    ("sign of the parity volume", "const int s = V > 0 ? 1 : -1;", "const int s = V > 0 ? -1 : 1;"),
+    ("sign of the parity volume", "if (V != 0) s = V > 0 ? 1 : -1;", "if (V != 0) s = V > 0 ? -1 : 1;"),
     ("swapped edge-bin slots of a tetrahedron",
      "Tup6 t = {g.bin[p1], g.bin[p2], g.bin[al], g.bin[q12], g.bin[be], g.bin[ga]};",
      "Tup6 t = {g.bin[p1], g.bin[p2], g.bin[al], g.bin[be], g.bin[q12], g.bin[ga]};"),
@@ -39,6 +40,12 @@ MUTANTS = [
     ("a weight factor repeated", "(i128)fw.W[i] * fw.W[j] * fw.W[ka]", "(i128)fw.W[i] * fw.W[j] * fw.W[j]"),
     ("lattice rounding instead of flooring", "(int64_t)std::floor(pos[i] * 1024.0)",
      "(int64_t)std::round(pos[i] * 1024.0)"),
+    ("pixel sector edge on the diagonal on the wrong side", "if (b >= a) ++sub;",
+     "if (b > a) ++sub;"),
+    ("pixel bands shifted by one edge", "if (z_at_least(z, n2, k - 8)) ++band;",
+     "if (z_at_least(z, n2, k - 7)) ++band;"),
+    ("pixel parity without the relabelling sign",
+     "s = (Vp > 0 ? 1 : -1) * pi.sign;", "s = (Vp > 0 ? 1 : -1);"),
 ]
 
 
