@@ -489,7 +489,8 @@ def measure_4pcf(gs, torch, runs=2):
 def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
     """The rows beyond the core path, each timed with CUDA events after one
     warm-up call: the equilateral 3pCF on the randoms' graph of the default
-    workload (beside the full 3pCF kernel time), the signed-weight connected
+    workload (beside the full 3pCF kernel time), the pixelised-direction
+    parity 4pCF on the 2e5-point 4pCF workload, the signed-weight connected
     4pCF on 1e5 data + 1e5 randoms, and the configuration tooling."""
     import ctypes
 
@@ -517,6 +518,21 @@ def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
         "alg_bytes_per_launch": 4 * words,
         "achieved_gbs": 4 * words / (km.value / 1e3) / 1e9 if km.value else None}
     g.close()
+
+    # pixelised-direction parity 4pCF on the 2e5-point 4pCF workload
+    s4 = catalogs.draw("ns200k_L400_r30_nb8")
+    p4 = torch.from_numpy(s4["pos"]).cuda()
+    g4 = gs.gs_build_graph(gs.gs_quantize(p4, s4["box_u"], True), s4["box_u"], s4["edges_u"])
+    kp = ctypes.c_double(0.0)
+    (ev, od), ms = timed(lambda: gs.gs_count_4pcf_parity_pix(g4, like=p4, kernel_ms=kp))
+    _, od_exact = gs.gs_count_4pcf_parity(g4, like=p4)
+    tet4 = float(ev.sum().item())
+    out["parity_pix"] = {
+        "workload": "ns200k_L400_r30_nb8", "call_ms": ms, "kernel_ms": kp.value,
+        "tetrahedra": tet4, "quadruplets_per_s": tet4 / (ms / 1e3),
+        "odd_abs_sum": float(od.abs().sum().item()),
+        "odd_abs_sum_exact_channel": float(od_exact.abs().sum().item())}
+    g4.close()
 
     spec = catalogs.draw("ns100k_r100k_L400_r30_nb8")
     bu, e4 = spec["box_u"], spec["edges_u"]

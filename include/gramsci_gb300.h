@@ -301,6 +301,38 @@ int gs_count_4pcf_parity(const gs_graph* g, const float* w, uint64_t* even, int6
                          double* weven, double* wodd, const gs_options* options);
 
 /*
+ * gs_count_4pcf_parity_pix - parity 4pCF with pixelised spoke directions
+ * (Sec. 3.2: the direction of each spoke is quantised to a pixel on the
+ * unit sphere, one byte per edge, and tetrahedra whose pixel volume is below
+ * 1e-9 in magnitude are degenerate and left out of the odd channel). The
+ * pixel scheme, which the paper leaves open, is fixed here as 256 equal-area
+ * pixels (see gs_direction_pixels). For each tetrahedron the three spokes
+ * run from its vertex with the smallest caller index to the other three in
+ * ascending caller index; V is (u1 x u2) . u3 of their pixel centres in
+ * FP64; odd gets sign(V) times the parity of the relabelling onto the orbit
+ * representative when the orbit is chiral and |V| >= 1e-9; a spoke of zero
+ * length (coincident points) makes the tetrahedron degenerate.
+ *   even, weven: as gs_count_4pcf_parity (identical values).
+ *   odd, wodd:   the pixelised odd channel.
+ * Errors: as gs_count_4pcf_parity.
+ */
+int gs_count_4pcf_parity_pix(const gs_graph* g, const float* w, uint64_t* even, int64_t* odd,
+                             double* weven, double* wodd, const gs_options* options);
+
+/*
+ * gs_direction_pixels - the direction pixel of gs_count_4pcf_parity_pix for
+ * integer vectors (Sec. 3.2's pixel byte): 16 bands of width 1/8 in
+ * cos(theta) = z / |d| on [-1, 1] times 16 sectors of pi/8 in
+ * phi = atan2(y, x) in [0, 2 pi); a direction on a band or sector edge
+ * belongs to the band or sector above it; sector 0 on the z axis; pixel =
+ * 16 band + sector. Decided exactly in integers on the device.
+ *   dirs    int32 [n][3] nonzero vectors (host or device), |components| < 2^20.
+ *   pixels  uint8 [n] out (host or device).
+ * Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA.
+ */
+int gs_direction_pixels(const int32_t* dirs, int64_t n, uint8_t* pixels, const gs_options* options);
+
+/*
  * gs_disconnected_4pcf - internal 2pCF and disconnected 4pCF on the same
  * graph (Sec. 3.3, Eq. disc), one sweep over the edges.
  *   w          NULL or float32 [n] weights (pair sums use w_i w_j, exact).

@@ -729,14 +729,18 @@ static int count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, do
               const Perm4& pi = conf->perms[conf->perm[raw]];
               int s = 0;
               if (pixel) {
+                // a spoke of zero length (coincident points) has no direction:
+                // the tetrahedron is degenerate
                 int px[3];
+                bool zero = false;
                 const int64_t u[3] = {j1, j2, j3};
                 for (int k = 0; k < 3; ++k) {
                   int64_t d[3];
                   displacement(g, i, u[k], d);
+                  zero = zero || (d[0] == 0 && d[1] == 0 && d[2] == 0);
                   px[k] = direction_pixel(d[0], d[1], d[2]);
                 }
-                const double Vp = pixel_volume(px[0], px[1], px[2]);
+                const double Vp = zero ? 0.0 : pixel_volume(px[0], px[1], px[2]);
                 if (std::fabs(Vp) >= kDegenerateVolume) s = (Vp > 0 ? 1 : -1) * pi.sign;
               } else {
                 int64_t d[3][3];

@@ -23,7 +23,8 @@ from . import build as _build
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
     "gs_graph_info", "gs_graph_tri_words", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_3pcf_equilateral", "gs_count_4pcf",
-    "gs_count_4pcf_parity", "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_config_mask_cm",
+    "gs_count_4pcf_parity", "gs_count_4pcf_parity_pix", "gs_direction_pixels",
+    "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_config_mask_cm",
     "gs_rebin_3pcf", "gs_rebin_4pcf", "gs_num_configs", "gs_config_bins",
     "gs_free_graph", "gs_strerror", "gs_kernel_launches", "gs_server", "gs_plan", "lib_path",
 ]
@@ -93,6 +94,8 @@ def _load():
         "gs_plan_wait": ([P, P], ci),
         "gs_plan_destroy": ([P], None),
         "gs_count_4pcf_parity": ([P, P, P, P, P, P, OP], ci),
+        "gs_count_4pcf_parity_pix": ([P, P, P, P, P, P, OP], ci),
+        "gs_direction_pixels": ([P, ctypes.c_int64, P, OP], ci),
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
         "gs_connected_4pcf": ([P, P, P, P, P, P, P, P, P, OP], ci),
         "gs_count_3pcf_equilateral": ([P, P, P, P, OP], ci),
@@ -333,8 +336,10 @@ def gs_count_4pcf(g: Graph, w=None, counts=None, wsum=None, like=None, **opts):
     return (counts, wsum) if w is not None else counts
 
 
-def gs_count_4pcf_parity(g: Graph, w=None, like=None, **opts):
-    """(even u64, odd i64) or, with weights, (even, odd, weven, wodd)."""
+def gs_count_4pcf_parity(g: Graph, w=None, like=None, pix=False, **opts):
+    """(even u64, odd i64) or, with weights, (even, odd, weven, wodd).
+    pix=True: the odd channel from pixelised spoke directions
+    (gs_count_4pcf_parity_pix)."""
     nc = gs_num_configs(4, g.nb)
     ref = like if like is not None else w
     even = _empty_like_input(ref, (nc,), np.uint64)
@@ -342,9 +347,27 @@ def gs_count_4pcf_parity(g: Graph, w=None, like=None, **opts):
     we = _empty_like_input(ref, (nc,), np.float64) if w is not None else None
     wo = _empty_like_input(ref, (nc,), np.float64) if w is not None else None
     o = _options(**opts)
-    _check(_lib.gs_count_4pcf_parity(g.handle, _ptr(w), _ptr(even), _ptr(odd), _ptr(we), _ptr(wo),
-                                     ctypes.byref(o)), "gs_count_4pcf_parity")
+    fn, name = ((_lib.gs_count_4pcf_parity_pix, "gs_count_4pcf_parity_pix") if pix else
+                (_lib.gs_count_4pcf_parity, "gs_count_4pcf_parity"))
+    _check(fn(g.handle, _ptr(w), _ptr(even), _ptr(odd), _ptr(we), _ptr(wo), ctypes.byref(o)), name)
     return (even, odd, we, wo) if w is not None else (even, odd)
+
+
+def gs_count_4pcf_parity_pix(g: Graph, w=None, like=None, **opts):
+    """Parity 4pCF with the odd channel from pixelised spoke directions."""
+    return gs_count_4pcf_parity(g, w, like=like, pix=True, **opts)
+
+
+def gs_direction_pixels(dirs, **opts):
+    """Direction pixels (uint8) of integer vectors [n][3] (host or device)."""
+    if not _is_torch(dirs):
+        dirs = np.ascontiguousarray(dirs, dtype=np.int32)
+    n = int(dirs.shape[0])
+    out = _empty_like_input(dirs, (n,), np.uint8)
+    o = _options(**opts)
+    _check(_lib.gs_direction_pixels(_ptr(dirs), n, _ptr(out), ctypes.byref(o)),
+           "gs_direction_pixels")
+    return out
 
 
 def gs_disconnected_4pcf(g: Graph, w=None, rr=None, like=None, zeta=True, **opts):

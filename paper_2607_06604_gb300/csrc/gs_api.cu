@@ -724,7 +724,8 @@ int gs_count_3pcf_batch(const gs_graph* const* graphs, int32_t n_graphs, const f
 }
 
 static int count4_common(const gs_graph* G, const float* w, bool parity, uint64_t* even,
-                         int64_t* odd, double* weven, double* wodd, const gs_options* options) {
+                         int64_t* odd, double* weven, double* wodd, const gs_options* options,
+                         bool pix = false) {
   if (!G || !even) return GS_EINVAL;
   const Graph& g = G->g;
   const Opts o = read_opts(options);
@@ -744,7 +745,7 @@ static int count4_common(const gs_graph* G, const float* w, bool parity, uint64_
     double* dwe = weven ? (is_device_ptr(weven) ? weven : sc.alloc<double>(nc)) : nullptr;
     double* dwo = wodd ? (is_device_ptr(wodd) ? wodd : sc.alloc<double>(nc)) : nullptr;
     if (!de || (odd && !dod) || (weven && !dwe) || (wodd && !dwo)) return GS_ENOMEM;
-    st = count4_device(g, w ? &fw : nullptr, parity, de, dod, dwe, dwo, o, sc);
+    st = count4_device(g, w ? &fw : nullptr, parity, de, dod, dwe, dwo, o, sc, pix);
     OutBuf outs[4] = {{even, de, sizeof(uint64_t) * nc},
                       {odd, dod, sizeof(int64_t) * nc},
                       {weven, dwe, sizeof(double) * nc},
@@ -767,6 +768,31 @@ int gs_count_4pcf_parity(const gs_graph* G, const float* w, uint64_t* even, int6
                          double* weven, double* wodd, const gs_options* options) {
   if (!odd) return GS_EINVAL;
   return count4_common(G, w, true, even, odd, weven, wodd, options);
+}
+
+int gs_count_4pcf_parity_pix(const gs_graph* G, const float* w, uint64_t* even, int64_t* odd,
+                             double* weven, double* wodd, const gs_options* options) {
+  if (!odd) return GS_EINVAL;
+  return count4_common(G, w, true, even, odd, weven, wodd, options, true);
+}
+
+int gs_direction_pixels(const int32_t* dirs, int64_t n, uint8_t* pixels,
+                        const gs_options* options) {
+  if (n < 0 || (n > 0 && (!dirs || !pixels))) return GS_EINVAL;
+  const Opts o = read_opts(options);
+  int st = GS_OK;
+  {
+    Scratch sc(o.stream);
+    const int32_t* dd = static_cast<const int32_t*>(to_device(sc, dirs, sizeof(int32_t) * 3 * n, o.stream));
+    uint8_t* dp = is_device_ptr(pixels) ? pixels : sc.alloc<uint8_t>(n > 0 ? n : 1);
+    if (n > 0 && (!dd || !dp)) return GS_ENOMEM;
+    st = direction_pixels_device(dd, n, dp, o.stream);
+    if (!st && n > 0 && dp != pixels)
+      st = cuda_status(cudaMemcpyAsync(pixels, dp, (size_t)n, cudaMemcpyDeviceToHost, o.stream));
+    cudaError_t e = cudaStreamSynchronize(o.stream);
+    if (!st) st = cuda_status(e);
+  }
+  return st;
 }
 
 int gs_disconnected_4pcf(const gs_graph* G, const float* w, const double* rr, uint64_t* pairs,

@@ -22,6 +22,9 @@
 // 64-bit atomics. Hubs with more than kMaxSmemRow neighbours run in a
 // second launch whose per-hub workspace lives in global scratch.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
 #include <type_traits>
 
 #include "gs_internal.cuh"
@@ -59,6 +62,7 @@ struct Args {
   unsigned long long* weven;  // [n_orbits][3] 192-bit
   unsigned long long* wodd;
   const int64_t* __restrict__ W;
+  const int8_t* __restrict__ pixsign;  // pixelised parity: signs of sorted pixel triples
   unsigned long long* hub_counter;
   int* err;
   unsigned char* gscratch;  // per-CTA global workspace
@@ -120,11 +124,65 @@ __device__ inline int64_t det3(const int4& da, const int4& db, const int4& dc) {
   }
 }
 
+// Direction pixel of the pixelised parity channel (Sec. 3.2 stores one
+// pixel byte per spoke and treats |V| < 1e-9 as degenerate; the scheme is
+// fixed here as 256 equal-area pixels): 16 bands of width 1/8 in
+// cos(theta) = z / |d| (a direction on a band edge belongs to the band
+// above it) times 16 sectors of pi / 8 in phi = atan2(y, x) in [0, 2 pi)
+// (an edge belongs to the sector above it; sector 0 on the z axis); pixel =
+// 16 band + sector. Everything is decided with exact 64-bit integer
+// comparisons: z / |d| against s / 8 through 64 z^2 against s^2 |d|^2, and
+// phi within its quadrant against pi/8, pi/4, 3pi/8 through tan(pi/8) =
+// sqrt(2) - 1 and tan(3pi/8) = sqrt(2) + 1 squared out.
+__host__ __device__ inline int dir_pixel(int64_t x, int64_t y, int64_t z) {
+  const int64_t n2 = x * x + y * y + z * z, z64 = 64 * z * z;
+  int band = z >= 0 ? 8 : 0;
+  for (int s = 1; s <= 7; ++s) {
+    const int64_t edge = (int64_t)(s * s) * n2;
+    // z >= 0: edges s/8 at or below z/|d|; z < 0: edges -s/8 at or below it
+    band += (z >= 0 ? (z64 >= edge) : (z64 <= edge)) ? 1 : 0;
+  }
+  int sector = 0;
+  if (x != 0 || y != 0) {
+    // turn by -pi/2 until the direction lies in [0, pi/2): a > 0, b >= 0
+    int quarter = 0;
+    int64_t a = x, b = y;
+    while (!(a > 0 && b >= 0)) {
+      const int64_t t = a;
+      a = b;
+      b = -t;
+      ++quarter;
+    }
+    const int64_t a2 = 2 * a * a;
+    int eighth = 0;
+    if ((a + b) * (a + b) >= a2) ++eighth;           // phi >= pi/8
+    if (b >= a) ++eighth;                            // phi >= pi/4
+    if (b > a && (b - a) * (b - a) >= a2) ++eighth;  // phi >= 3pi/8
+    sector = 4 * quarter + eighth;
+  }
+  return 16 * band + sector;
+}
+
+// Sign of the pixel volume (u_p1 x u_p2) . u_p3 of three pixel centres: 0
+// for repeated pixels, else the table entry of the sorted triple times the
+// parity of the sort. The table (host-built in FP64, 0 where |V| < 1e-9) is
+// indexed by the combinatorial number C(r,3) + C(q,2) + p of p < q < r.
+__device__ inline int pix_sign(const int8_t* __restrict__ T, int p1, int p2, int p3) {
+  if (p1 == p2 || p1 == p3 || p2 == p3) return 0;
+  int s = 1;
+  if (p1 > p2) { const int t = p1; p1 = p2; p2 = t; s = -s; }
+  if (p2 > p3) { const int t = p2; p2 = p3; p3 = t; s = -s; }
+  if (p1 > p2) { const int t = p1; p1 = p2; p2 = t; s = -s; }
+  const int idx = p3 * (p3 - 1) * (p3 - 2) / 6 + p2 * (p2 - 1) / 2 + p1;
+  return s * (int)T[idx];
+}
+
 struct Workspace {
   uint32_t* row;      // staged N+(i) words
   int4* disp;         // displacement of each neighbour from the hub
   unsigned long long* table;  // hash: (id << 32) | local index, empty = ~0
   uint32_t* bits;     // m x W bit matrix
+  int* cid;           // caller index of each neighbour (pixelised parity)
   uint32_t* queue;    // per-warp (b, c) queue: kWarps x 64 words, then kWarps x 64 bytes
 };
 
@@ -141,6 +199,8 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
   p += (size_t)(1 << tbits) * 8;
   w.bits = reinterpret_cast<uint32_t*>(p);
   p += (size_t)cap * Wc * 4;
+  w.cid = reinterpret_cast<int*>(p);
+  p += (size_t)cap * 4;
   w.queue = reinterpret_cast<uint32_t*>(p);
   return w;
 }
@@ -149,7 +209,7 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
 // tetrahedra. GW: the workspace is in global memory (rows above the shared
 // capacity) and counts go straight to the global histograms. Returns false
 // when the staging copy timed out.
-template <bool PARITY, bool WEIGHTED, bool SMALLR, bool GW, class E2T>
+template <bool PARITY, bool WEIGHTED, bool SMALLR, bool GW, bool PIX, class E2T>
 __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uint8_t* bk,
                      unsigned* h_even,
                      int* h_odd, int64_t i, int m, uint64_t* bar, uint32_t& phase, int* s_row) {
@@ -189,6 +249,7 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     // gives a vertex's displacement and b_i,vertex
     w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
                           (int)mi((int64_t)Q.z - P.z, a.box), (int)edge_bin(row[k]));
+    if (PIX) w.cid[k] = Q.w;
     uint32_t h = (id * kHashMul) >> shift;
     const unsigned long long ent = ((unsigned long long)id << 32) | (unsigned)k;
     while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
@@ -272,9 +333,46 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
             atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
           }
           if (PARITY && (ent >> 31)) {
-            const int64_t V = det3<SMALLR>(da, db, dc);
-            if (V != 0) {
-              int sgn = V > 0 ? 1 : -1;
+            int sgn;
+            if constexpr (PIX) {
+              // the pixelised reading: the three spokes from the vertex with
+              // the smallest caller index, taken in ascending caller order; a
+              // sorting network keeps the displacements (from the hub) and
+              // the parity of the reordering
+              int key[4] = {P.w, w.cid[sa], w.cid[sb], w.cid[sc]};
+              int4 D[4] = {make_int4(0, 0, 0, 0), da, db, dc};
+              int par = 1;
+              auto cx = [&](int u, int v) {
+                if (key[u] > key[v]) {
+                  const int tk = key[u];
+                  key[u] = key[v];
+                  key[v] = tk;
+                  const int4 td = D[u];
+                  D[u] = D[v];
+                  D[v] = td;
+                  par = -par;
+                }
+              };
+              cx(0, 1);
+              cx(2, 3);
+              cx(0, 2);
+              cx(1, 3);
+              cx(1, 2);
+              int px[3];
+              bool zero = false;  // coincident points: no direction, degenerate
+#pragma unroll
+              for (int t = 1; t <= 3; ++t) {
+                const int64_t x = (int64_t)D[t].x - D[0].x, y = (int64_t)D[t].y - D[0].y,
+                              z = (int64_t)D[t].z - D[0].z;
+                zero = zero || (x == 0 && y == 0 && z == 0);
+                px[t - 1] = dir_pixel(x, y, z);
+              }
+              sgn = zero ? 0 : par * pix_sign(a.pixsign, px[0], px[1], px[2]);
+            } else {
+              const int64_t V = det3<SMALLR>(da, db, dc);
+              sgn = V > 0 ? 1 : (V < 0 ? -1 : 0);
+            }
+            if (sgn != 0) {
               if ((ent >> 30) & 1u) sgn = -sgn;
               if (GW) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
               else atomicAdd(h_odd + orbit, sgn);
@@ -338,7 +436,7 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
   return true;
 }
 
-template <bool PARITY, bool WEIGHTED, bool SMALLR>
+template <bool PARITY, bool WEIGHTED, bool SMALLR, bool PIX>
 __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using E2T = typename std::conditional<SMALLR, uint32_t, int64_t>::type;
@@ -437,11 +535,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     const int m = a.deg[i];
     bool ok;
     if (m > a.thr)
-      ok = hub4<PARITY, WEIGHTED, SMALLR, true>(a, ws_g, e2, bk, h_even, h_odd, i, m, &bar, phase,
-                                                &s_row);
+      ok = hub4<PARITY, WEIGHTED, SMALLR, true, PIX>(a, ws_g, e2, bk, h_even, h_odd, i, m, &bar,
+                                                     phase, &s_row);
     else
-      ok = hub4<PARITY, WEIGHTED, SMALLR, false>(a, ws_s, e2, bk, h_even, h_odd, i, m, &bar, phase,
-                                                 &s_row);
+      ok = hub4<PARITY, WEIGHTED, SMALLR, false, PIX>(a, ws_s, e2, bk, h_even, h_odd, i, m, &bar,
+                                                      phase, &s_row);
     if (!ok) return;
   }
   __syncthreads();
@@ -453,7 +551,7 @@ size_t workspace_bytes(int mcap) {
   while ((1 << tbits) < 2 * mcap) ++tbits;
   const size_t Wc = (size_t)(mcap + 31) / 32;
   return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + ((size_t)1 << tbits) * 8 +
-         (size_t)mcap * Wc * 4 + (size_t)kWarps * 64 * 5 + 64;
+         (size_t)mcap * Wc * 4 + (size_t)mcap * 4 + (size_t)kWarps * 64 * 5 + 64;
 }
 
 }  // namespace
@@ -466,10 +564,86 @@ __global__ void k_i64_to_double(const long long* c, int64_t n, double* out) {
     out[k] = (double)c[k];
 }
 
+namespace {
+// Signs of the pixel volume of every sorted pixel triple p < q < r (0 below
+// 1e-9 in magnitude), built once on the host in FP64 and copied to each
+// device on first use.
+std::mutex g_pix_mu;
+std::vector<int8_t> g_pix_host;
+int8_t* g_pix_dev[64] = {nullptr};
+
+const int8_t* pixel_sign_table(int* status) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) {
+    *status = GS_ERANGE;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_pix_mu);
+  if (g_pix_dev[dev]) return g_pix_dev[dev];
+  if (g_pix_host.empty()) {
+    double u[256][3];
+    for (int p = 0; p < 256; ++p) {
+      const double zc = (2.0 * (p >> 4) + 1.0) / 16.0 - 1.0;
+      const double phi = M_PI * (2.0 * (p & 15) + 1.0) / 16.0;
+      const double rho = std::sqrt((1.0 - zc) * (1.0 + zc));
+      u[p][0] = rho * std::cos(phi);
+      u[p][1] = rho * std::sin(phi);
+      u[p][2] = zc;
+    }
+    g_pix_host.resize((size_t)256 * 255 * 254 / 6);
+    size_t idx = 0;
+    for (int r = 0; r < 256; ++r)
+      for (int q = 0; q < r; ++q)
+        for (int p = 0; p < q; ++p, ++idx) {
+          const double* a = u[p];
+          const double* b = u[q];
+          const double* c = u[r];
+          const double v = (a[1] * b[2] - a[2] * b[1]) * c[0] + (a[2] * b[0] - a[0] * b[2]) * c[1] +
+                           (a[0] * b[1] - a[1] * b[0]) * c[2];
+          g_pix_host[idx] = std::fabs(v) < 1e-9 ? 0 : (v > 0 ? 1 : -1);
+        }
+  }
+  int8_t* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, g_pix_host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(d, g_pix_host.data(), g_pix_host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (d) cudaFree(d);
+    *status = cuda_status(e);
+    return nullptr;
+  }
+  g_pix_dev[dev] = d;
+  return d;
+}
+
+__global__ void k_dir_pixels(const int32_t* d, int64_t n, uint8_t* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (uint8_t)dir_pixel(d[3 * k], d[3 * k + 1], d[3 * k + 2]);
+}
+}  // namespace
+
+int direction_pixels_device(const int32_t* d_dirs, int64_t n, uint8_t* d_out, cudaStream_t s) {
+  if (n > 0) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    k_dir_pixels<<<blocks, 256, 0, s>>>(d_dirs, n, d_out);
+    note_launch();
+  }
+  return cuda_status(cudaGetLastError());
+}
+
 int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
-                  int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc) {
+                  int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc,
+                  bool pix) {
   cudaStream_t s = o.stream;
   int st = GS_OK;
+  pix = pix && parity;
+  const int8_t* pixsign = nullptr;
+  if (pix) {
+    pixsign = pixel_sign_table(&st);
+    if (!pixsign) return st;
+  }
   const Conf4Tables* t = conf4_tables(g.nb, &st);
   if (!t) return st;
   const int no = (int)t->n_orbits;
@@ -497,6 +671,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
                           : sc.alloc<unsigned long long>(no))
                  : nullptr;
   a.W = weighted ? fw->d_W : nullptr;
+  a.pixsign = pixsign;
   a.weven = weighted ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
   a.wodd = (weighted && parity) ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
   a.hub_counter = sc.alloc<unsigned long long>(2);
@@ -526,14 +701,18 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
 
   const bool small_r = g.edges[g.nb] < 32768;
   auto pick = [&]() -> void (*)(Args) {
-#define GS_PICK(P, Wt)                                                       \
-  return small_r ? k_count4<P, Wt, true> : k_count4<P, Wt, false>
-    if (parity) {
-      if (weighted) GS_PICK(true, true);
-      GS_PICK(true, false);
+#define GS_PICK(P, Wt, X)                                                    \
+  return small_r ? k_count4<P, Wt, true, X> : k_count4<P, Wt, false, X>
+    if (parity && pix) {
+      if (weighted) GS_PICK(true, true, true);
+      GS_PICK(true, false, true);
     }
-    if (weighted) GS_PICK(false, true);
-    GS_PICK(false, false);
+    if (parity) {
+      if (weighted) GS_PICK(true, true, false);
+      GS_PICK(true, false, false);
+    }
+    if (weighted) GS_PICK(false, true, false);
+    GS_PICK(false, false, false);
 #undef GS_PICK
   };
   // variant 1 sends every hub to the global workspace (exercises it on any

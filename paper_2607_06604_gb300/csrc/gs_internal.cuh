@@ -164,8 +164,11 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
                   const Opts& o, Scratch& sc, bool equi = false);
 int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
                         double* const* d_wsum, const Opts& o, Scratch& sc);
+// pix: the odd channel from pixelised spoke directions (parity only)
 int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
-                  int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc);
+                  int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc,
+                  bool pix = false);
+int direction_pixels_device(const int32_t* d_dirs, int64_t n, uint8_t* d_out, cudaStream_t s);
 int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint64_t* d_pairs,
                       double* d_xi, double* d_zeta, const Opts& o, Scratch& sc);
 int connected_device(const Graph& gdr, const FixedW& fdr, const Graph& gr, const FixedW& fr,

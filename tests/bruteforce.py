@@ -260,8 +260,10 @@ def count4_pixel(X, box_u, edges_u):
         k, chiral = conf[rep]
         even[k] += 1
         if chiral:
-            pix = [direction_pixel(*(int(t) for t in d[v[0], v[m]])) for m in (1, 2, 3)]
-            V = pixel_volume(*pix)
+            spokes = [tuple(int(t) for t in d[v[0], v[m]]) for m in (1, 2, 3)]
+            if any(s == (0, 0, 0) for s in spokes):
+                continue  # coincident points: no direction, degenerate
+            V = pixel_volume(*(direction_pixel(*s) for s in spokes))
             if abs(V) >= 1e-9:
                 odd[k] += (1 if V > 0 else -1) * perm_sign(p)
     return even, odd
