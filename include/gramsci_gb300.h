@@ -184,9 +184,12 @@ int gs_graph_export(const gs_graph* g, int64_t* ptr, int32_t* deg, int32_t* nbr,
  *   w       NULL (unweighted) or float32 [n] weights in caller order.
  *   counts  uint64 [C(nb+2,3)] triangle counts per configuration.
  *   wsum    NULL or float64 [C(nb+2,3)]: sum of w_i w_j w_k per
- *           configuration, accumulated exactly and rounded once.
- * Errors: GS_EINVAL, GS_EUNSUPPORTED (weights not finite, or spanning so
- * many binades that the exact sums would not fit), GS_ETIMEOUT, GS_ECUDA.
+ *           configuration, accumulated exactly and rounded once to the
+ *           nearest double (ties to even). Weights whose magnitudes span
+ *           more than about 2^5 are split exactly (W = A + 2^27 B) and the
+ *           sums of four exact evaluations interpolated: four launches.
+ * Errors: GS_EINVAL, GS_EUNSUPPORTED (weights not finite, or magnitudes
+ * spanning more than about 2^28), GS_ETIMEOUT, GS_ECUDA.
  */
 int gs_count_3pcf(const gs_graph* g, const float* w, uint64_t* counts, double* wsum,
                   const gs_options* options);
@@ -279,8 +282,10 @@ int gs_count_3pcf_equilateral(const gs_graph* g, const float* w, uint64_t* count
 /*
  * gs_count_4pcf - binned tetrahedron counts (Sec. 2.2, Sec. 3.1.1):
  * tetrahedra whose six pairs are all edges, one count per S4 orbit.
- *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact).
- * Errors: as gs_count_3pcf; GS_ERANGE when nb > 16.
+ *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact;
+ *   weights spanning more than about 2^5: five launches, as for the 3pCF).
+ * Errors: as gs_count_3pcf (the weight span limit is about 2^26); GS_ERANGE
+ * when nb > 16.
  */
 int gs_count_4pcf(const gs_graph* g, const float* w, uint64_t* counts, double* wsum,
                   const gs_options* options);

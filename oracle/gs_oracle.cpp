@@ -40,8 +40,9 @@
 // above the hub; tetrahedra with the three-pointer walk of Eq. (threeway).
 // Weighted sums are accumulated exactly: every FP32 weight is an integer
 // multiple of a common power of two, products are formed in 128-bit
-// integers and summed in a 256-bit accumulator, and the exact total is
-// rounded to FP64 once at the end, to nearest with ties to even.
+// integers when they fit and exactly in 256 bits otherwise, summed in a
+// 256-bit accumulator, and the exact total is rounded to FP64 once at the
+// end, to nearest with ties to even.
 //
 // Host threads partition hubs; each thread has its own histograms, summed
 // at the end (the shape of the paper's OpenMP CPU kernels, Sec. 4.3).
@@ -92,6 +93,43 @@ struct Acc256 {
       w[k] = s2;
       carry = c1 | c2;
     }
+  }
+  // The exact product a * b of two signed 128-bit integers (below 2^254 in
+  // magnitude), as a 256-bit two's-complement value.
+  static Acc256 product(i128 a, i128 b) {
+    typedef unsigned __int128 u128;
+    const bool neg = (a < 0) != (b < 0);
+    const u128 ua = a < 0 ? (u128)0 - (u128)a : (u128)a;
+    const u128 ub = b < 0 ? (u128)0 - (u128)b : (u128)b;
+    const uint64_t a0 = (uint64_t)ua, a1 = (uint64_t)(ua >> 64);
+    const uint64_t b0 = (uint64_t)ub, b1 = (uint64_t)(ub >> 64);
+    // schoolbook: limb k collects the partial products a_x b_y with x + y = k
+    uint64_t limb[4] = {0, 0, 0, 0};
+    auto put = [&](int k, u128 v) {
+      for (; k < 4 && v; ++k) {
+        const u128 t = (u128)limb[k] + (uint64_t)v;
+        limb[k] = (uint64_t)t;
+        v = (v >> 64) + (t >> 64);
+      }
+    };
+    put(0, (u128)a0 * b0);
+    put(1, (u128)a0 * b1);
+    put(1, (u128)a1 * b0);
+    put(2, (u128)a1 * b1);
+    Acc256 r;
+    for (int k = 0; k < 4; ++k) r.w[k] = limb[k];
+    return neg ? r.negated() : r;
+  }
+  Acc256 negated() const {
+    Acc256 r;
+    unsigned carry = 1;
+    for (int k = 0; k < 4; ++k) {
+      const uint64_t x = ~w[k];
+      const uint64_t s2 = x + carry;
+      carry = (s2 < x) ? 1u : 0u;
+      r.w[k] = s2;
+    }
+    return r;
   }
   // Bit k of the magnitude m (k outside [0, 256) reads as 0).
   static unsigned bit_of(const uint64_t m[4], int k) {
@@ -626,11 +664,14 @@ int or_count_3pcf(void* gp, const float* w, uint64_t* counts, double* wsum, int6
   FixedWeights fw;
   if (w) {
     fw = make_fixed(w, g.n);
-    if (!fw.ok || 3 * (fw.bits + 1) > 126) return -2;
+    // |W| < 2^53: W_i W_j fits 128 bits; the triple product is formed in
+    // 128 bits when it fits, else exactly in 256 bits
+    if (!fw.ok || fw.bits > 53) return -2;
   }
   if (hub_hi < 0 || hub_hi > g.n) hub_hi = g.n;
   if (hub_lo < 0) hub_lo = 0;
   const int nt = std::max(1, nthreads);
+  const bool narrow = 3 * (fw.bits + 1) <= 126;
   std::vector<std::vector<uint64_t>> hc(nt, std::vector<uint64_t>(nconf, 0));
   std::vector<std::vector<Acc256>> hw(w ? nt : 0, std::vector<Acc256>(nconf));
   parallel_for(std::max<int64_t>(0, hub_hi - hub_lo), nt, [&](int64_t t, int tid) {
@@ -647,7 +688,10 @@ int or_count_3pcf(void* gp, const float* w, uint64_t* counts, double* wsum, int6
         if (ka == kb) {
           const int c = conf.of(b_ij, g.bin[a], g.bin[b]);
           hc[tid][c] += 1;
-          if (w) hw[tid][c].add((i128)fw.W[i] * fw.W[j] * fw.W[ka]);
+          if (w) {
+            if (narrow) hw[tid][c].add((i128)fw.W[i] * fw.W[j] * fw.W[ka]);
+            else hw[tid][c].add(Acc256::product((i128)fw.W[i] * fw.W[j], (i128)fw.W[ka]));
+          }
           ++a;
           ++b;
         } else if (ka < kb) {
@@ -686,7 +730,9 @@ static int count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, do
   FixedWeights fw;
   if (w) {
     fw = make_fixed(w, g.n);
-    if (!fw.ok || 4 * (fw.bits + 1) > 126) return -2;
+    // |W| < 2^52: a product of four weights and the sum of up to 2^46 of
+    // them stay inside the 256-bit accumulator
+    if (!fw.ok || fw.bits > 52) return -2;
   }
   const int nt = std::max(1, nthreads);
   std::vector<std::vector<uint64_t>> he(nt, std::vector<uint64_t>(nconf, 0));
@@ -718,9 +764,9 @@ static int count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, do
             const size_t raw = conf->encode(t);
             const int o = conf->orbit[raw];
             he[tid][o] += 1;
-            i128 prod = 0;
+            Acc256 prod;
             if (w) {
-              prod = (i128)fw.W[i] * fw.W[j1] * fw.W[j2] * fw.W[j3];
+              prod = Acc256::product((i128)fw.W[i] * fw.W[j1], (i128)fw.W[j2] * fw.W[j3]);
               hwe[tid][o].add(prod);
             }
             if (conf->chiral[o]) {
@@ -753,7 +799,7 @@ static int count_4pcf(void* gp, const float* w, uint64_t* even, int64_t* odd, do
               }
               if (s != 0) {
                 ho[tid][o] += s;
-                if (w) hwo[tid][o].add(s > 0 ? prod : -prod);
+                if (w) hwo[tid][o].add(s > 0 ? prod : prod.negated());
               }
             }
             ++al;

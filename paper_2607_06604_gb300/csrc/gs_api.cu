@@ -395,7 +395,8 @@ __global__ void k_weight_fixed(const float* w, const int4* xyzp, int64_t n, int 
 }
 }  // namespace
 
-int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cudaStream_t s) {
+int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cudaStream_t s,
+                    int max_bits) {
   const float* dw = static_cast<const float*>(to_device(sc, w, sizeof(float) * g.n, s));
   int* flags = sc.alloc<int>(4);
   int64_t* W = sc.alloc<int64_t>(g.n);
@@ -412,10 +413,61 @@ int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cu
   out->scale = 24 - h[0];
   out->bits = 25 + (h[1] - h[0]) + 1;
   out->nonneg = h[3] == 0;
-  if (out->bits > 31) return GS_EUNSUPPORTED;
+  if (out->bits > max_bits) return GS_EUNSUPPORTED;
   { k_weight_fixed<<<304, 256, 0, s>>>(dw, g.d_xyzp, g.n, out->scale, W); note_launch(); }
   out->d_W = W;
   return cuda_status(cudaGetLastError());
+}
+
+// Wide weights: the sums of degree-3 (triangles) or degree-4 (tetrahedra)
+// weight products evaluated exactly at t = 0, 1, -1, 2[, -2] on the split
+// weights A + t B, then interpolated and rounded once (csrc/gs_wide.cu).
+int count3_wide(const Graph& g, const FixedW& fw, uint64_t* d_counts, double* d_wsum,
+                const Opts& o, Scratch& sc) {
+  const int64_t nc = num_conf3(g.nb);
+  const int npts = 4;
+  unsigned long long* P = sc.alloc<unsigned long long>(3 * (size_t)nc * npts);
+  int64_t* Wt = sc.alloc<int64_t>(g.n > 0 ? g.n : 1);
+  if (!P || !Wt) return GS_ENOMEM;
+  FixedW ft;
+  ft.d_W = Wt;
+  ft.scale = fw.scale;
+  ft.bits = 30;
+  ft.nonneg = false;
+  int st = GS_OK;
+  for (int k = 0; k < npts && !st; ++k) {
+    st = split_weights_device(fw, g.n, wide_eval_point(k), Wt, o.stream);
+    if (!st) st = count3_device(g, &ft, d_counts, nullptr, o, sc, false, P + 3 * (size_t)nc * k);
+  }
+  if (!st) st = combine_wide_device(P, nc, 3, 3 * fw.scale, d_wsum, o.stream);
+  return st;
+}
+
+int count4_wide(const Graph& g, const FixedW& fw, bool parity, bool pix, uint64_t* d_even,
+                int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc) {
+  int st = GS_OK;
+  const Conf4Tables* t = conf4_tables(g.nb, &st);
+  if (!t) return st;
+  const int64_t no = t->n_orbits;
+  const int npts = 5;
+  unsigned long long* Pe = sc.alloc<unsigned long long>(3 * (size_t)no * npts);
+  unsigned long long* Po = parity ? sc.alloc<unsigned long long>(3 * (size_t)no * npts) : nullptr;
+  int64_t* Wt = sc.alloc<int64_t>(g.n > 0 ? g.n : 1);
+  if (!Pe || (parity && !Po) || !Wt) return GS_ENOMEM;
+  FixedW ft;
+  ft.d_W = Wt;
+  ft.scale = fw.scale;
+  ft.bits = 30;
+  ft.nonneg = false;
+  for (int k = 0; k < npts && !st; ++k) {
+    st = split_weights_device(fw, g.n, wide_eval_point(k), Wt, o.stream);
+    if (!st)
+      st = count4_device(g, &ft, parity, d_even, d_odd, nullptr, nullptr, o, sc, pix,
+                         Pe + 3 * (size_t)no * k, parity ? Po + 3 * (size_t)no * k : nullptr);
+  }
+  if (!st && d_weven) st = combine_wide_device(Pe, no, 4, 4 * fw.scale, d_weven, o.stream);
+  if (!st && d_wodd && parity) st = combine_wide_device(Po, no, 4, 4 * fw.scale, d_wodd, o.stream);
+  return st;
 }
 
 }  // namespace gs
@@ -661,13 +713,16 @@ int gs_count_3pcf(const gs_graph* G, const float* w, uint64_t* counts, double* w
     Scratch sc(o.stream);
     FixedW fw;
     if (w) {
-      st = prepare_weights(g, w, &fw, sc, o.stream);
+      st = prepare_weights(g, w, &fw, sc, o.stream, 54);
       if (st) return st;
     }
     uint64_t* dc = is_device_ptr(counts) ? counts : sc.alloc<uint64_t>(nc);
     double* dw = wsum ? (is_device_ptr(wsum) ? wsum : sc.alloc<double>(nc)) : nullptr;
     if (!dc || (wsum && !dw)) return GS_ENOMEM;
-    st = count3_device(g, w ? &fw : nullptr, dc, dw, o, sc);
+    if (w && wsum && fw.bits > kNarrowWeightBits)
+      st = count3_wide(g, fw, dc, dw, o, sc);
+    else
+      st = count3_device(g, w ? &fw : nullptr, dc, dw, o, sc);
     if (!st && dc != counts)
       st = cuda_status(cudaMemcpyAsync(counts, dc, sizeof(uint64_t) * nc, cudaMemcpyDeviceToHost, o.stream));
     if (!st && dw && dw != wsum)
@@ -737,7 +792,7 @@ static int count4_common(const gs_graph* G, const float* w, bool parity, uint64_
     Scratch sc(o.stream);
     FixedW fw;
     if (w) {
-      st = prepare_weights(g, w, &fw, sc, o.stream);
+      st = prepare_weights(g, w, &fw, sc, o.stream, 52);
       if (st) return st;
     }
     uint64_t* de = is_device_ptr(even) ? even : sc.alloc<uint64_t>(nc);
@@ -745,7 +800,10 @@ static int count4_common(const gs_graph* G, const float* w, bool parity, uint64_
     double* dwe = weven ? (is_device_ptr(weven) ? weven : sc.alloc<double>(nc)) : nullptr;
     double* dwo = wodd ? (is_device_ptr(wodd) ? wodd : sc.alloc<double>(nc)) : nullptr;
     if (!de || (odd && !dod) || (weven && !dwe) || (wodd && !dwo)) return GS_ENOMEM;
-    st = count4_device(g, w ? &fw : nullptr, parity, de, dod, dwe, dwo, o, sc, pix);
+    if (w && fw.bits > kNarrowWeightBits)
+      st = count4_wide(g, fw, parity, pix, de, dod, dwe, dwo, o, sc);
+    else
+      st = count4_device(g, w ? &fw : nullptr, parity, de, dod, dwe, dwo, o, sc, pix);
     OutBuf outs[4] = {{even, de, sizeof(uint64_t) * nc},
                       {odd, dod, sizeof(int64_t) * nc},
                       {weven, dwe, sizeof(double) * nc},

@@ -1336,9 +1336,10 @@ __global__ void k_u64_to_double(const unsigned long long* c, int64_t n, double* 
 int resolve_variant(const Graph& g, int wmode, int variant);
 
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
-                  const Opts& o_in, Scratch& sc, bool equi) {
+                  const Opts& o_in, Scratch& sc, bool equi, unsigned long long* wacc_out) {
   Opts o = o_in;
-  o.variant = equi ? std::max(o.variant, 0) : resolve_variant(g, (fw && d_wsum) ? 2 : 0, o.variant);
+  const bool weighted = fw && (d_wsum || wacc_out);
+  o.variant = equi ? std::max(o.variant, 0) : resolve_variant(g, weighted ? 2 : 0, o.variant);
   cudaStream_t s = o.stream;
   // the equilateral configurations (b, b, b) are indexed by b
   const int nconf = equi ? g.nb : (int)num_conf3(g.nb);
@@ -1361,8 +1362,9 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   a.stage_cap = (o.variant & 2) ? 0 : kStageCap;
   a.one.counts = reinterpret_cast<unsigned long long*>(d_counts);
   a.one.W = fw ? fw->d_W : nullptr;
-  const int wm = (fw && d_wsum) ? kExact : kNone;
-  a.one.wacc = wm == kExact ? sc.alloc<unsigned long long>(3 * (size_t)nconf) : nullptr;
+  const int wm = weighted ? kExact : kNone;
+  a.one.wacc = wm == kExact ? (wacc_out ? wacc_out : sc.alloc<unsigned long long>(3 * (size_t)nconf))
+                            : nullptr;
   a.hub_counter = sc.alloc<unsigned long long>(1);
   a.err = sc.alloc<int>(1);
   if (!a.hub_counter || !a.err || (wm == kExact && !a.one.wacc)) return GS_ENOMEM;

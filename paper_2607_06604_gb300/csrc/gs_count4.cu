@@ -635,7 +635,7 @@ int direction_pixels_device(const int32_t* d_dirs, int64_t n, uint8_t* d_out, cu
 
 int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
                   int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc,
-                  bool pix) {
+                  bool pix, unsigned long long* weven_out, unsigned long long* wodd_out) {
   cudaStream_t s = o.stream;
   int st = GS_OK;
   pix = pix && parity;
@@ -672,8 +672,10 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
                  : nullptr;
   a.W = weighted ? fw->d_W : nullptr;
   a.pixsign = pixsign;
-  a.weven = weighted ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
-  a.wodd = (weighted && parity) ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
+  a.weven = weighted ? (weven_out ? weven_out : sc.alloc<unsigned long long>(3 * (size_t)no))
+                     : nullptr;
+  a.wodd = (weighted && parity) ? (wodd_out ? wodd_out : sc.alloc<unsigned long long>(3 * (size_t)no))
+                                : nullptr;
   a.hub_counter = sc.alloc<unsigned long long>(2);
   a.err = sc.alloc<int>(1);
   if (!a.hub_counter || !a.err || (parity && !a.odd) || (weighted && !a.weven) ||

@@ -154,20 +154,38 @@ struct FixedW {
   int bits = 0;  // max bit length of |W_i| plus one sign bit
   bool nonneg = true;  // no weight is negative
 };
-int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cudaStream_t s);
+// max_bits: the widest |W| (bits, sign included) the caller can sum exactly:
+// 31 for the kernels' direct path, up to 54 where the caller splits wide
+// weights (below); wider weights give GS_EUNSUPPORTED.
+int prepare_weights(const Graph& g, const float* w, FixedW* out, Scratch& sc, cudaStream_t s,
+                    int max_bits = 31);
+constexpr int kNarrowWeightBits = 31;
+
+// Wide weights (csrc/gs_wide.cu): out = A + t B with W = A + 2^27 B,
+// 0 <= A < 2^27; and the exact interpolation of degree-3 or degree-4 sums
+// evaluated at t = 0, 1, -1, 2[, -2] (blocks of n 192-bit sums in d_P), at
+// t = 2^27, rounded once to double with the given scale.
+int split_weights_device(const FixedW& fw, int64_t n, int t, int64_t* d_out, cudaStream_t s);
+int combine_wide_device(const unsigned long long* d_P, int64_t n, int degree, int scale,
+                        double* d_out, cudaStream_t s);
+int wide_eval_point(int k);
 
 // Kernel launchers (defined in the per-stage .cu files).
 int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
                        const std::vector<int64_t>& edges, const Opts& o, Graph* g);
 // equi: the equilateral configurations (b, b, b) only, nb outputs.
+// wacc_out: NULL, or n_conf 192-bit accumulators that receive the exact
+// weighted sums (zeroed here) instead of a rounded d_wsum.
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
-                  const Opts& o, Scratch& sc, bool equi = false);
+                  const Opts& o, Scratch& sc, bool equi = false,
+                  unsigned long long* wacc_out = nullptr);
 int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
                         double* const* d_wsum, const Opts& o, Scratch& sc);
 // pix: the odd channel from pixelised spoke directions (parity only)
 int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_even,
                   int64_t* d_odd, double* d_weven, double* d_wodd, const Opts& o, Scratch& sc,
-                  bool pix = false);
+                  bool pix = false, unsigned long long* weven_out = nullptr,
+                  unsigned long long* wodd_out = nullptr);
 int direction_pixels_device(const int32_t* d_dirs, int64_t n, uint8_t* d_out, cudaStream_t s);
 int pairs_disc_device(const Graph& g, const FixedW* fw, const double* d_rr, uint64_t* d_pairs,
                       double* d_xi, double* d_zeta, const Opts& o, Scratch& sc);

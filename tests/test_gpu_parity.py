@@ -267,6 +267,55 @@ def test_3pcf_pair_kernel_binning_modes(gs, torch_mod, rmin, rmax, nb):
         assert np.array_equal(gs.gs_count_3pcf(g, variant=variant), rc), variant
 
 
+def wide_weights(n, seed, span_log2=20):
+    """FP32 weights whose magnitudes span 2^span_log2 (log-uniform), both signs."""
+    rng = np.random.default_rng(seed)
+    mag = np.exp2(rng.uniform(-span_log2 / 2, span_log2 / 2, size=n)) * rng.uniform(0.5, 1.5, n)
+    return (mag * np.where(rng.random(n) < 0.3, -1.0, 1.0)).astype(np.float32)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_3pcf_wide_weights(gs, torch_mod, periodic):
+    """Weights spanning 2^20 take the split-weight path (exact sums of the
+    products of A + t B at four points t, interpolated and rounded once):
+    bit for bit the oracle's exact sums, on both triangle kernels."""
+    L = 120.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(20_000, L, seed=171, sigma=2.0, periodic=periodic)
+    X = oracle.quantize(pos, box_u, periodic)
+    w = wide_weights(len(X), seed=172)
+    assert np.abs(w).max() / np.abs(w).min() > 2 ** 19
+    edges = catalogs.bin_edges_u(0.0, 12.0, 8)
+    bu = box_u if periodic else 0
+    rc, rw = oracle.Graph(X, bu, edges).count_3pcf(w)
+    g = gs.gs_build_graph(X, bu, edges)
+    for variant in (0, 512):
+        gc, gw = gs.gs_count_3pcf(g, w, variant=variant)
+        assert np.array_equal(gc, rc) and np.array_equal(gw, rw), variant
+    gc, gw = gs.gs_count_3pcf(g, dev(torch_mod, w))
+    assert np.array_equal(gw.cpu().numpy(), rw)
+
+
+def test_4pcf_wide_weights(gs, torch_mod):
+    box_u = 80_000
+    rng = np.random.default_rng(181)
+    X = np.concatenate([rng.integers(0, box_u, size=(4000, 3)),
+                        np.mod(40_000 + rng.integers(-5000, 5001, size=(300, 3)), box_u)])
+    X = X.astype(np.int32)
+    w = wide_weights(X.shape[0], seed=182)
+    edges = np.array([0, 2500, 5000, 7000], dtype=np.int64)
+    og = oracle.Graph(X, box_u, edges)
+    re, ro, rwe, rwo = og.count_4pcf(w)
+    ge, go, gwe, gwo = run4(gs, torch_mod, X, box_u, edges, w)
+    assert np.array_equal(ge, re) and np.array_equal(go, ro)
+    assert np.array_equal(gwe, rwe) and np.array_equal(gwo, rwo)
+    pe, po, pwe, pwo = og.count_4pcf(w, pixel=True)
+    g = gs.gs_build_graph(X, box_u, edges)
+    qe, qo, qwe, qwo = gs.gs_count_4pcf_parity_pix(g, w)
+    assert np.array_equal(qe, pe) and np.array_equal(qo, po)
+    assert np.array_equal(qwe, pwe) and np.array_equal(qwo, pwo)
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 5])
 def test_3pcf_tiny_and_empty(gs, torch_mod, n):
     box_u = 100_000

@@ -152,6 +152,37 @@ def test_3pcf_signed_weights_exact():
     assert np.array_equal(ws, ref_w)
 
 
+def wide_weights(n, seed, span_log2=20):
+    """FP32 weights whose magnitudes span 2^span_log2 (log-uniform), both signs."""
+    rng = np.random.default_rng(seed)
+    mag = np.exp2(rng.uniform(-span_log2 / 2, span_log2 / 2, size=n)) * rng.uniform(0.5, 1.5, n)
+    return (mag * np.where(rng.random(n) < 0.3, -1.0, 1.0)).astype(np.float32)
+
+
+def test_3pcf_wide_weights_exact():
+    """Weights spanning 2^20 (products beyond 128 bits): exact sums equal the
+    rational all-triples sums bit for bit."""
+    box_u = 30_000
+    edges_u = np.array([0, 2500, 5000, 7000], dtype=np.int64)
+    X = clustered_lattice(100, box_u, 17, 4000)
+    w = wide_weights(X.shape[0], seed=18)
+    assert np.abs(w).max() / np.abs(w).min() > 2 ** 18
+    ref_c, ref_w = bf.count3(X, box_u, edges_u, w)
+    c, ws = oracle.Graph(X, box_u, edges_u, nthreads=2).count_3pcf(w)
+    assert np.array_equal(c, ref_c) and np.array_equal(ws, ref_w)
+
+
+def test_4pcf_wide_weights_exact():
+    box_u = 20_000
+    edges_u = np.array([0, 2000, 4000], dtype=np.int64)
+    X = clustered_lattice(60, box_u, 23, 2500)
+    w = wide_weights(X.shape[0], seed=24)
+    e_ref, o_ref, we_ref, wo_ref = bf.count4(X, box_u, edges_u, w)
+    e, o, we, wo = oracle.Graph(X, box_u, edges_u).count_4pcf(w)
+    assert np.array_equal(e, e_ref) and np.array_equal(o, o_ref)
+    assert np.array_equal(we, we_ref) and np.array_equal(wo, wo_ref)
+
+
 def test_3pcf_poisson_closed_form():
     """Unbinned triangle total of a uniform periodic catalogue.
 
