@@ -605,19 +605,28 @@ def measure_mocks(gs, torch, count, nmax, grid):
     xyz = [gs.gs_quantize(p, box_u, True) for p in mocks]
     del mocks
     kinds = [4 if k < 32 else 3 for k in range(count)]
-    # a) one catalogue at a time through the plain API
+    # a) one catalogue at a time through the plain API; the device time of
+    # each call's main kernels is summed to show where the wall time goes
+    import ctypes
+    km = ctypes.c_double(0.0)
+    busy = {"build_ms": 0.0, "count3_ms": 0.0, "count4_ms": 0.0}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plain, plain4 = [], {}
     for k, X in enumerate(xyz):
-        g = gs.gs_build_graph(X, box_u, e3)
-        plain.append(gs.gs_count_3pcf(g))
+        g = gs.gs_build_graph(X, box_u, e3, kernel_ms=km)
+        busy["build_ms"] += km.value
+        plain.append(gs.gs_count_3pcf(g, kernel_ms=km))
+        busy["count3_ms"] += km.value
         g.close()
         if kinds[k] == 4:
-            g4 = gs.gs_build_graph(X, box_u, e4)
-            plain4[k] = gs.gs_count_4pcf_parity(g4)
+            g4 = gs.gs_build_graph(X, box_u, e4, kernel_ms=km)
+            busy["build_ms"] += km.value
+            plain4[k] = gs.gs_count_4pcf_parity(g4, kernel_ms=km)
+            busy["count4_ms"] += km.value
             g4.close()
     t_plain = time.perf_counter() - t0
+    busy_total_s = sum(busy.values()) / 1e3
     tri = float(sum(int(c.sum()) for c in plain))
     tet = float(sum(int(e.sum()) for e, _ in plain4.values()))
 
@@ -655,6 +664,8 @@ def measure_mocks(gs, torch, count, nmax, grid):
             "box": L, "rmax3": 60.0, "nb3": 12, "rmax4": 25.0, "nb4": 6, "also_4pcf": min(32, count),
             "triangles": tri, "tetrahedra": tet, "host_generation_s": t_gen,
             "one_at_a_time_s": t_plain, "one_at_a_time_catalogues_per_s": count / t_plain,
+            "one_at_a_time_kernel_ms": busy,
+            "one_at_a_time_kernel_busy_fraction": busy_total_s / t_plain,
             "served_saturated_s": t_sat, "served_catalogues_per_s": capacity,
             "speedup_vs_one_at_a_time": t_plain / t_sat,
             "poisson_rate_per_s": 0.8 * capacity, "poisson_span_s": t_poi,

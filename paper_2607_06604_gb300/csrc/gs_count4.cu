@@ -6,10 +6,10 @@
 // persistent CTA
 //   1. stages N+(i) in shared memory with a bulk (TMA) copy, with the
 //      minimum-image displacement of every neighbour from i;
-//   2. builds a hash id -> local index and, with one warp per spoke a,
-//      streams N+(j_a) and sets bit c of row a of an m x m bit matrix for
-//      every c > a adjacent to a (the paper's per-hub connectivity matrix,
-//      Sec. 3.5.2, as bits);
+//   2. builds the m x m bit matrix of adjacency within N+(i) (the paper's
+//      per-hub connectivity matrix, Sec. 3.5.2, as bits) by testing every
+//      pair (a, c), a < c, of staged displacements against the edge
+//      distances, a ballot per 32-bit word;
 //   3. for every triangle (a, b), b a bit of row a, takes the common bits
 //      of rows a and b above b: each is a tetrahedron (i, a, b, c). This is
 //      the three-way walk of Eq. (threeway) done 32 candidates per word.
@@ -180,23 +180,18 @@ __device__ inline int pix_sign(const int8_t* __restrict__ T, int p1, int p2, int
 struct Workspace {
   uint32_t* row;      // staged N+(i) words
   int4* disp;         // displacement of each neighbour from the hub
-  unsigned long long* table;  // hash: (id << 32) | local index, empty = ~0
   uint32_t* bits;     // m x W bit matrix
   int* cid;           // caller index of each neighbour (pixelised parity)
   uint32_t* queue;    // per-warp (b, c) queue: kWarps x 64 words, then kWarps x 64 bytes
 };
 
 __device__ inline Workspace carve(unsigned char* p, int cap) {
-  int tbits = 5;
-  while ((1 << tbits) < 2 * cap) ++tbits;
   const int Wc = (cap + 31) / 32;
   Workspace w;
   w.row = reinterpret_cast<uint32_t*>(p);
   p += (size_t)pad_row(cap) * 4;
   w.disp = reinterpret_cast<int4*>(p);
   p += (size_t)cap * 16;
-  w.table = reinterpret_cast<unsigned long long*>(p);
-  p += (size_t)(1 << tbits) * 8;
   w.bits = reinterpret_cast<uint32_t*>(p);
   p += (size_t)cap * Wc * 4;
   w.cid = reinterpret_cast<int*>(p);
@@ -223,10 +218,6 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
   } else {
     row = grow;
   }
-  int tbits = 5;
-  while ((1 << tbits) < 2 * m) ++tbits;
-  const int T = 1 << tbits, shift = 32 - tbits;
-  for (int k = tid; k < T; k += kThreads) w.table[k] = ~0ull;
   for (int k = tid; k < m * W; k += kThreads) w.bits[k] = 0u;
   if (!GW) {
     const bool ok = mbar_wait(bar, phase, kWaitLimit);
@@ -250,41 +241,27 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
                           (int)mi((int64_t)Q.z - P.z, a.box), (int)edge_bin(row[k]));
     if (PIX) w.cid[k] = Q.w;
-    uint32_t h = (id * kHashMul) >> shift;
-    const unsigned long long ent = ((unsigned long long)id << 32) | (unsigned)k;
-    while (atomicCAS(w.table + h, ~0ull, ent) != ~0ull) h = (h + 1) & (T - 1);
   }
   __syncthreads();
   if (tid == 0) *s_row = 0;
-  // bit matrix: row a gets bit c for every c > a adjacent to j_a
-  const uint32_t hub_hi = edge_id(row[m - 1]);
+  // bit matrix: row a gets bit c for every c > a whose distance from a is an
+  // edge's, E_0^2 <= |D_c - D_a|^2 < E_nb^2 on the staged hub-relative
+  // displacements (4 E_nb < L makes their difference the pair's minimum
+  // image); a warp per row, a ballot per 32-bit word
+  const int64_t e2lo = (int64_t)e2[0], e2hi = (int64_t)e2[nb];
   for (int sa = warp; sa < m - 1; sa += kWarps) {
-    const uint32_t j = edge_id(row[sa]);
-    const uint32_t* rj = row_at(a.adj, a.ptr, j, a.adj_off, a.split, a.adj_off2);
-    const int dj4 = (int)pad_row(a.deg[j]);
-    for (int t0 = 0; t0 < dj4; t0 += 128) {
-      const int t = t0 + lane * 4;
-      const uint4 v = (t < dj4) ? ldg_nc_v4(rj + t)
-                                : make_uint4(kSentinel, kSentinel, kSentinel, kSentinel);
-      const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const uint32_t key = edge_id(vv[qq]);
-        if (key > hub_hi) continue;
-        uint32_t h = (key * kHashMul) >> shift;
-        for (;;) {
-          const unsigned long long e = w.table[h];
-          if (e == ~0ull) break;
-          if ((uint32_t)(e >> 32) == key) {
-            const int c = (int)(e & 0xffffffffu);
-            atomicOr(w.bits + sa * W + (c >> 5), 1u << (c & 31));
-            break;
-          }
-          h = (h + 1) & (T - 1);
-        }
+    const int4 da = w.disp[sa];
+    for (int c0 = (sa + 1) & ~31; c0 < m; c0 += 32) {
+      const int c = c0 + lane;
+      bool edge = false;
+      if (c > sa && c < m) {
+        const int4 dc = w.disp[c];
+        const int x = dc.x - da.x, y = dc.y - da.y, z = dc.z - da.z;
+        const long long D2 = (long long)x * x + (long long)y * y + (long long)z * z;
+        edge = D2 >= e2lo && D2 < e2hi;
       }
-      const uint32_t last = __shfl_sync(0xffffffffu, v.w, 31);
-      if (edge_id(last) > hub_hi) break;
+      const uint32_t word = __ballot_sync(0xffffffffu, edge);
+      if (lane == 0) w.bits[sa * W + (c0 >> 5)] = word;
     }
   }
   __syncthreads();
@@ -547,11 +524,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
 }
 
 size_t workspace_bytes(int mcap) {
-  int tbits = 5;
-  while ((1 << tbits) < 2 * mcap) ++tbits;
   const size_t Wc = (size_t)(mcap + 31) / 32;
-  return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + ((size_t)1 << tbits) * 8 +
-         (size_t)mcap * Wc * 4 + (size_t)mcap * 4 + (size_t)kWarps * 64 * 5 + 64;
+  return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + (size_t)mcap * Wc * 4 +
+         (size_t)mcap * 4 + (size_t)kWarps * 64 * 5 + 64;
 }
 
 }  // namespace
