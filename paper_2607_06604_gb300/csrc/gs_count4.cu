@@ -182,7 +182,9 @@ struct Workspace {
   int4* disp;         // displacement of each neighbour from the hub
   uint32_t* bits;     // m x W bit matrix
   int* cid;           // caller index of each neighbour (pixelised parity)
-  uint32_t* queue;    // per-warp (b, c) queue: kWarps x 64 words, then kWarps x 64 bytes
+  uint8_t* brow;      // per warp: bin(a, c) of its current row a, cap bytes each
+  uint32_t* queue;    // per-warp queue of (b, c) entries: kWarps x 64 words
+  int cap;
 };
 
 __device__ inline Workspace carve(unsigned char* p, int cap) {
@@ -196,7 +198,10 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
   p += (size_t)cap * Wc * 4;
   w.cid = reinterpret_cast<int*>(p);
   p += (size_t)cap * 4;
+  w.brow = reinterpret_cast<uint8_t*>(p);
+  p += (size_t)kWarps * ((cap + 15) & ~15);
   w.queue = reinterpret_cast<uint32_t*>(p);
+  w.cap = (cap + 15) & ~15;
   return w;
 }
 
@@ -271,7 +276,6 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
   // batch of 32 entries is processed one tetrahedron per lane
   const int64_t Wi = WEIGHTED ? a.W[i] : 0;
   uint32_t* qbc = w.queue + warp * 64;
-  uint8_t* qb12 = reinterpret_cast<uint8_t*>(w.queue + kWarps * 64) + warp * 64;
   // rows near the start of N+(i) carry most of the work: warps take rows
   // from a shared counter (reset by thread 0 before the bit matrix was built)
   for (;;) {
@@ -284,19 +288,26 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     const int4 da = w.disp[sa];
     const int64_t Wia = WEIGHTED ? Wi * a.W[edge_id(wa)] : 0;
     const uint32_t* bra = w.bits + sa * W;
+    // bin(a, c) of every edge (a, c) of the row, once per row: the triangle
+    // loop and the drain read b_12 and b_13 from here
+    uint8_t* brw = w.brow + (size_t)warp * w.cap;
+    for (int c = sa + 1 + lane; c < m; c += 32)
+      if ((bra[c >> 5] >> (c & 31)) & 1u)
+        brw[c] = (uint8_t)bin_of(d2<SMALLR>(da, w.disp[c]), e2, nb, bk, a.bk_shift);
+    __syncwarp();
     int qn = 0;
     // process the first 32 queue entries (or all when draining)
     auto drain = [&](bool all) {
       while (qn >= 32 || (all && qn > 0)) {
         const bool active = lane < qn;
         const uint32_t e = active ? qbc[lane] : 0u;
-        const int b12 = active ? (int)qb12[lane] : 0;
         __syncwarp();
         if (active) {
           const int sb = (int)(e >> 16), sc = (int)(e & 0xFFFFu);
+          const int b12 = brw[sb];
           const int4 db = w.disp[sb], dc = w.disp[sc];
           const int b02 = db.w, b03 = dc.w;
-          const int b13 = bin_of(d2<SMALLR>(da, dc), e2, nb, bk, a.bk_shift);
+          const int b13 = brw[sc];
           const int b23 = bin_of(d2<SMALLR>(db, dc), e2, nb, bk, a.bk_shift);
           const uint32_t ent =
               a.lut[(((uint32_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
@@ -367,16 +378,9 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
         if (qn >= 32) {  // keep the overflow (the queue holds at most 63)
           const int rest = qn - 32;
           uint32_t mv = 0;
-          uint8_t mb = 0;
-          if (lane < rest) {
-            mv = qbc[32 + lane];
-            mb = qb12[32 + lane];
-          }
+          if (lane < rest) mv = qbc[32 + lane];
           __syncwarp();
-          if (lane < rest) {
-            qbc[lane] = mv;
-            qb12[lane] = mb;
-          }
+          if (lane < rest) qbc[lane] = mv;
           __syncwarp();
           qn = rest;
         } else {
@@ -389,18 +393,13 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
       while (xb) {  // warp-uniform: every lane walks the same bits
         const int sb = wb0 * 32 + __ffs(xb) - 1;
         xb &= xb - 1u;
-        const int b12 = bin_of(d2<SMALLR>(da, w.disp[sb]), e2, nb, bk, a.bk_shift);
         const uint32_t* brb = w.bits + sb * W;
         for (int wc = sb >> 5; wc < W; ++wc) {
           uint32_t x = bra[wc] & brb[wc];
           if (wc == (sb >> 5)) x &= ~((2u << (sb & 31)) - 1u);
           if (!x) continue;
           const bool set = (x >> lane) & 1u;
-          if (set) {
-            const int slot = qn + __popc(x & ((1u << lane) - 1u));
-            qbc[slot] = ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
-            qb12[slot] = (uint8_t)b12;
-          }
+          if (set) qbc[qn + __popc(x & ((1u << lane) - 1u))] = ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
           qn += __popc(x);
           __syncwarp();
           drain(false);
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
 size_t workspace_bytes(int mcap) {
   const size_t Wc = (size_t)(mcap + 31) / 32;
   return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + (size_t)mcap * Wc * 4 +
-         (size_t)mcap * 4 + (size_t)kWarps * 64 * 5 + 64;
+         (size_t)mcap * 4 + (size_t)kWarps * ((mcap + 15) & ~15) + (size_t)kWarps * 64 * 5 + 64;
 }
 
 }  // namespace
