@@ -85,22 +85,42 @@ def measured_peaks():
 KERNEL_VERSION = "k_count3p.v1"  # bump when k_count3 changes; stale captures then report null
 
 
+KERNEL4_VERSION = "k_count4.v3"  # likewise for k_count4
+
+
+def _profile_values(name):
+    p = os.path.join(ROOT, "profiles", name)
+    vals = {}
+    if os.path.exists(p):
+        for line in open(p):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.strip()
+    return vals
+
+
 def recorded_traffic():
     """Per-launch DRAM bytes of the counting kernel from the committed ncu
     summary, or None when that capture predates the current kernel."""
-    p = os.path.join(ROOT, "profiles", "count3_traffic.txt")
-    if not os.path.exists(p):
-        return None
-    vals = {}
-    for line in open(p):
-        if "=" in line and not line.startswith("#"):
-            k, v = line.split("=", 1)
-            vals[k.strip()] = v.strip()
+    vals = _profile_values("count3_traffic.txt")
     if vals.get("kernel_version") != KERNEL_VERSION:
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])
     except (KeyError, ValueError):
+        return None
+
+
+def recorded_traffic4(edges):
+    """Per-launch DRAM bytes of k_count4 scaled from the committed capture by
+    the edge count, or None when that capture predates the current kernel."""
+    vals = _profile_values("count4_traffic.txt")
+    if vals.get("kernel_version") != KERNEL4_VERSION:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_profile_case"]) * edges / \
+            float(vals["edges_profile_case"])
+    except (KeyError, ValueError, ZeroDivisionError):
         return None
 
 
@@ -478,7 +498,8 @@ def measure_4pcf(gs, torch, runs=2):
             "pair_sweep_gbs": info["edge_slots"] * 4 / (pk.value / 1e3) / 1e9 if pk.value else None,
             "odd_abs_sum": float(odd.abs().sum().item()),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": recorded_traffic4(info["edges"]),
+                         "peak_kind": peak_kind,
                          "kernel": "k_count4 (parity)", "alg_bytes_per_launch": b4,
                          "per_unit": "5 B per edge: hub rows, spoke rows, and the row of each "
                                      "triangle's third vertex",
