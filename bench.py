@@ -51,7 +51,8 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-4pcf", action="store_true",
                     help="skip the secondary 4pCF + parity measurement")
-    ap.add_argument("--profile", choices=["count3", "count3w", "count4", "pairs", "equi3w"],
+    ap.add_argument("--profile", choices=["count3", "count3w", "count4", "count4w", "pairs",
+                                          "equi3w"],
                     default=None,
                     help="run one small case of one kernel for an ncu capture (no JSON)")
     ap.add_argument("--variant", type=int, default=0,
@@ -762,8 +763,16 @@ def run_profile(args):
         pos = torch.from_numpy(catalogs.neyman_scott(100_000, L, seed=6, sigma=2.0)).cuda()
         edges = catalogs.bin_edges_u(0.0, 30.0, 8)
         g = gs.gs_build_graph(gs.gs_quantize(pos, box_u, True), box_u, edges)
+        # count4w: signed weights (40% negative), as in the connected estimator
+        rng = np.random.default_rng(7)
+        w = torch.from_numpy((catalogs.uniform_weights(100_000, seed=8) *
+                              np.where(rng.random(100_000) < 0.4, -1.0, 1.0))
+                             .astype(np.float32)).cuda()
         for _ in range(2):
-            gs.gs_count_4pcf_parity(g, like=pos)
+            if args.profile == "count4w":
+                gs.gs_count_4pcf_parity(g, w)
+            else:
+                gs.gs_count_4pcf_parity(g, like=pos)
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "info": gs.gs_graph_info(g)}))
 

@@ -21,6 +21,15 @@
 // that parity. Counts use per-CTA shared-memory histograms flushed with
 // 64-bit atomics. Hubs with more than kMaxSmemRow neighbours run in a
 // second launch whose per-hub workspace lives in global scratch.
+//
+// Weighted sums (exact, fixed-point W): the hub's sums of W_a W_b W_c are
+// kept per orbit in shared 128-bit words (two 64-bit atomics each), one for
+// each sign of the volume so that a tetrahedron adds to one word only, and
+// multiplied by W_i into the global 192-bit sums when the hub ends. Shared
+// memory holds these words (and the counts) only for the `hot` orbits: the
+// orbit tables are relabelled so that the orbits met most often in a
+// sample of hubs come first, and a tetrahedron of any other orbit goes
+// straight to the global sums with its full product.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -57,6 +66,8 @@ struct Args {
   int thr;    // hubs with more neighbours than this use the global workspace
   int gcap;   // global workspace capacity (neighbours)
   int bk_shift, bk_n;  // squared-distance buckets (bk_n = 0: binary search)
+  int hot;             // orbits (slots) below this are accumulated in shared memory
+  int64_t hub_stride;  // hubs hub_begin + k hub_stride (1: every hub)
   unsigned long long* even;
   unsigned long long* odd;
   unsigned long long* weven;  // [n_orbits][3] 192-bit
@@ -177,11 +188,62 @@ __device__ inline int pix_sign(const int8_t* __restrict__ T, int p1, int p2, int
   return s * (int)T[idx];
 }
 
+// A 128-bit two's complement value (lo, hi) into a shared 128-bit sum kept
+// as two 64-bit words (sums modulo 2^128; the caller keeps the true sum in
+// range).
+__device__ inline void shared_add_i128(unsigned long long* p, unsigned long long lo,
+                                       unsigned long long hi) {
+  const unsigned long long o = atomicAdd(p, lo);
+  hi += (o + lo < o) ? 1ull : 0ull;
+  if (hi) atomicAdd(p + 1, hi);
+}
+
+// A 192-bit two's complement value into three global 64-bit words.
+__device__ inline void atomic_add_w192(unsigned long long* g, unsigned long long w0,
+                                       unsigned long long w1, unsigned long long w2) {
+  const unsigned long long o0 = atomicAdd(g, w0);
+  const unsigned long long c0 = (o0 + w0 < o0) ? 1ull : 0ull;
+  const unsigned long long s1 = w1 + c0;
+  const unsigned long long c1a = (s1 < w1) ? 1ull : 0ull;  // w1 = 2^64 - 1 and a carry
+  unsigned long long c1b = 0;
+  if (s1) {
+    const unsigned long long o1 = atomicAdd(g + 1, s1);
+    c1b = (o1 + s1 < o1) ? 1ull : 0ull;
+  }
+  const unsigned long long s2 = w2 + c1a + c1b;
+  if (s2) atomicAdd(g + 2, s2);
+}
+
+// S * Wi into a global 192-bit sum: S a signed 128-bit hub sum (lo, hi),
+// |Wi| < 2^63.
+__device__ inline void fold_i128(unsigned long long* g, unsigned long long lo,
+                                 unsigned long long hi, long long Wi) {
+  const bool sn = (long long)hi < 0, wn = Wi < 0;
+  if (sn) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  const unsigned long long v = wn ? (unsigned long long)(-Wi) : (unsigned long long)Wi;
+  unsigned long long p0 = lo * v;
+  const unsigned long long t = __umul64hi(lo, v);
+  unsigned long long p1 = hi * v + t;
+  unsigned long long p2 = __umul64hi(hi, v) + (p1 < t ? 1ull : 0ull);
+  if (sn != wn) {
+    p0 = ~p0 + 1ull;
+    unsigned long long c = p0 == 0ull ? 1ull : 0ull;
+    p1 = ~p1 + c;
+    c = (c && p1 == 0ull) ? 1ull : 0ull;
+    p2 = ~p2 + c;
+  }
+  atomic_add_w192(g, p0, p1, p2);
+}
+
 struct Workspace {
   uint32_t* row;      // staged N+(i) words
   int4* disp;         // displacement of each neighbour from the hub
   uint32_t* bits;     // m x W bit matrix
   int* cid;           // caller index of each neighbour (pixelised parity)
+  int* wv;            // weight of each neighbour (weighted sums)
   uint8_t* brow;      // per warp: bin(a, c) of its current row a, cap bytes each
   uint32_t* queue;    // per-warp queue of (b, c) entries: kWarps x 64 words
   int cap;
@@ -198,6 +260,8 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
   p += (size_t)cap * Wc * 4;
   w.cid = reinterpret_cast<int*>(p);
   p += (size_t)cap * 4;
+  w.wv = reinterpret_cast<int*>(p);
+  p += (size_t)cap * 4;
   w.brow = reinterpret_cast<uint8_t*>(p);
   p += (size_t)kWarps * ((cap + 15) & ~15);
   w.queue = reinterpret_cast<uint32_t*>(p);
@@ -209,10 +273,18 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
 // tetrahedra. GW: the workspace is in global memory (rows above the shared
 // capacity) and counts go straight to the global histograms. Returns false
 // when the staging copy timed out.
+// Shared cells per weighted slot: one (no parity) or three (V = 0, V > 0,
+// V < 0), each a u32 count and a 128-bit sum; even = all three, odd = the
+// second minus the third.
+template <bool PARITY>
+constexpr int kCat = PARITY ? 3 : 1;
+
+// h_even / h_odd: unweighted per-orbit counts; weighted, h_even holds the
+// cells' counts and h_sum their sums.
 template <bool PARITY, bool WEIGHTED, bool SMALLR, bool GW, bool PIX, class E2T>
 __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uint8_t* bk,
-                     unsigned* h_even,
-                     int* h_odd, int64_t i, int m, uint64_t* bar, uint32_t& phase, int* s_row) {
+                     unsigned* h_even, int* h_odd, unsigned long long* h_sum, int64_t i, int m,
+                     uint64_t* bar, uint32_t& phase, int* s_row) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = a.nb;
   const int W = (m + 31) / 32;
@@ -246,6 +318,7 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
                           (int)mi((int64_t)Q.z - P.z, a.box), (int)edge_bin(row[k]));
     if (PIX) w.cid[k] = Q.w;
+    if (WEIGHTED) w.wv[k] = (int)a.W[id];
   }
   __syncthreads();
   if (tid == 0) *s_row = 0;
@@ -286,7 +359,8 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     const uint32_t wa = row[sa];
     const int b01 = (int)edge_bin(wa);
     const int4 da = w.disp[sa];
-    const int64_t Wia = WEIGHTED ? Wi * a.W[edge_id(wa)] : 0;
+    const int64_t Wa = WEIGHTED ? (int64_t)w.wv[sa] : 0;
+    const int64_t Wia = Wi * Wa;
     const uint32_t* bra = w.bits + sa * W;
     // bin(a, c) of every edge (a, c) of the row, once per row: the triangle
     // loop and the drain read b_12 and b_13 from here
@@ -312,16 +386,10 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
           const uint32_t ent =
               a.lut[(((uint32_t)((b01 * nb + b02) * nb + b12) * nb + b03) * nb + b13) * nb + b23];
           const int orbit = (int)(ent & 0x3FFFFFFFu);
-          if (GW) atomicAdd(a.even + orbit, 1ull);
-          else atomicAdd(h_even + orbit, 1u);
-          long long plo = 0, phi = 0;
-          // (W_i W_a)(W_b W_c): two products below 2^60, one 128-bit product
-          if (WEIGHTED) {
-            mul_i128(Wia, a.W[edge_id(row[sb])] * a.W[edge_id(row[sc])], &plo, &phi);
-            atomic_add_i192(a.weven + 3 * orbit, (unsigned long long)plo, (unsigned long long)phi);
-          }
+          // the volume's sign, relabelled onto the orbit representative (0:
+          // achiral orbit or degenerate tetrahedron)
+          int sgn = 0;
           if (PARITY && (ent >> 31)) {
-            int sgn;
             if constexpr (PIX) {
               // the pixelised reading: the three spokes from the vertex with
               // the smallest caller index, taken in ascending caller order; a
@@ -360,18 +428,42 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
               const int64_t V = det3<SMALLR>(da, db, dc);
               sgn = V > 0 ? 1 : (V < 0 ? -1 : 0);
             }
-            if (sgn != 0) {
-              if ((ent >> 30) & 1u) sgn = -sgn;
-              if (GW) atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
-              else atomicAdd(h_odd + orbit, sgn);
-              if (WEIGHTED) {
-                unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
+            if ((ent >> 30) & 1u) sgn = -sgn;
+          }
+          // orbits below a.hot live in shared memory (every orbit when
+          // unweighted)
+          const bool hot = !GW && orbit < a.hot;
+          if (WEIGHTED) {
+            const int64_t Wbc = (int64_t)w.wv[sb] * w.wv[sc];  // below 2^60
+            long long plo, phi;
+            if (hot) {
+              // the hub's count and sum of W_a W_b W_c (below 2^90) in the
+              // orbit's cell for V = 0 / V > 0 / V < 0
+              const int cell = kCat<PARITY> * orbit + (sgn > 0 ? 1 : (sgn < 0 ? 2 : 0));
+              atomicAdd(h_even + cell, 1u);
+              mul_i128(Wa, Wbc, &plo, &phi);
+              shared_add_i128(h_sum + 2 * cell, (unsigned long long)plo, (unsigned long long)phi);
+            } else {
+              // (W_i W_a)(W_b W_c) straight into the global sums
+              atomicAdd(a.even + orbit, 1ull);
+              mul_i128(Wia, Wbc, &plo, &phi);
+              unsigned long long lo = (unsigned long long)plo, hi = (unsigned long long)phi;
+              atomic_add_i192(a.weven + 3 * orbit, lo, hi);
+              if (PARITY && sgn != 0) {
+                atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
                 if (sgn < 0) {  // negate the 128-bit product
                   lo = ~lo + 1ull;
                   hi = ~hi + (lo == 0ull ? 1ull : 0ull);
                 }
                 atomic_add_i192(a.wodd + 3 * orbit, lo, hi);
               }
+            }
+          } else {
+            if (hot) atomicAdd(h_even + orbit, 1u);
+            else atomicAdd(a.even + orbit, 1ull);
+            if (PARITY && sgn != 0) {
+              if (hot) atomicAdd(h_odd + orbit, sgn);
+              else atomicAdd(a.odd + orbit, (unsigned long long)(long long)sgn);
             }
           }
         }
@@ -425,18 +517,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   __shared__ int s_row;
 
   const int tid = threadIdx.x;
-  unsigned* h_even = reinterpret_cast<unsigned*>(smem);
-  int* h_odd = reinterpret_cast<int*>(h_even + a.n_orbits);
-  unsigned char* sws = smem + (size_t)a.n_orbits * 4 * (PARITY ? 2 : 1);
-  sws = reinterpret_cast<unsigned char*>(((uintptr_t)sws + 15) & ~(uintptr_t)15);
+  // shared slots of the orbits below a.hot: unweighted, the even and odd
+  // counts; weighted, kCat cells of a 128-bit sum (the hub's) and a count
+  const int nh = a.hot;
+  constexpr int nc = WEIGHTED ? kCat<PARITY> : 1;
+  unsigned char* sp = smem;
+  unsigned long long* h_sum = reinterpret_cast<unsigned long long*>(sp);
+  sp += WEIGHTED ? (size_t)nh * nc * 16 : 0;
+  unsigned* h_even = reinterpret_cast<unsigned*>(sp);
+  sp += (size_t)nh * nc * 4;
+  int* h_odd = reinterpret_cast<int*>(sp);
+  sp += (PARITY && !WEIGHTED) ? (size_t)nh * 4 : 0;
+  unsigned char* sws = reinterpret_cast<unsigned char*>(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   const Workspace ws_s = carve(sws, a.mcap);
   const Workspace ws_g = carve(a.gscratch ? a.gscratch + (size_t)blockIdx.x * a.gscratch_stride
                                           : sws,
                                a.gscratch ? a.gcap : a.mcap);
 
-  for (int k = tid; k < a.n_orbits; k += kThreads) {
+  for (int k = tid; k < nh * nc; k += kThreads) {
     h_even[k] = 0;
-    if (PARITY) h_odd[k] = 0;
+    if (PARITY && !WEIGHTED) h_odd[k] = 0;
+    if (WEIGHTED) h_sum[2 * k] = h_sum[2 * k + 1] = 0ull;
   }
   for (int b = tid; b <= a.nb; b += kThreads) e2[b] = (E2T)a.e2g[b];
   for (int k = tid; k < a.bk_n; k += kThreads) {
@@ -454,7 +555,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   uint32_t phase = 0;
 
   auto flush = [&]() {
-    for (int k = tid; k < a.n_orbits; k += kThreads) {
+    for (int k = tid; k < nh; k += kThreads) {
+      if (WEIGHTED) {
+        // cells V = 0, V > 0, V < 0: even = all three, odd = second - third
+        const unsigned c0 = h_even[nc * k];
+        const unsigned cp = PARITY ? h_even[nc * k + 1] : 0u;
+        const unsigned cn = PARITY ? h_even[nc * k + 2] : 0u;
+        if (c0 | cp | cn) {
+          atomicAdd(a.even + k, (unsigned long long)c0 + cp + cn);
+          if (PARITY && cp != cn)
+            atomicAdd(a.odd + k, (unsigned long long)((long long)cp - (long long)cn));
+          h_even[nc * k] = 0;
+          if (PARITY) h_even[nc * k + 1] = h_even[nc * k + 2] = 0;
+        }
+        continue;
+      }
       const unsigned c = h_even[k];
       if (c) {
         atomicAdd(a.even + k, (unsigned long long)c);
@@ -482,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
       } else {
         int64_t qq = q - a.nbig;
         for (;;) {
-          i = a.hub_begin + qq;
+          i = a.hub_begin + qq * a.hub_stride;
           d = (i < a.hub_end) ? a.deg[i] : 0;
           if (i >= a.hub_end || (d >= 3 && d <= a.thr)) break;
           qq = (int64_t)atomicAdd(a.hub_counter, 1ull) - a.nbig;
@@ -510,12 +625,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
     }
     const int m = a.deg[i];
     bool ok;
-    if (m > a.thr)
-      ok = hub4<PARITY, WEIGHTED, SMALLR, true, PIX>(a, ws_g, e2, bk, h_even, h_odd, i, m, &bar,
-                                                     phase, &s_row);
-    else
-      ok = hub4<PARITY, WEIGHTED, SMALLR, false, PIX>(a, ws_s, e2, bk, h_even, h_odd, i, m, &bar,
-                                                      phase, &s_row);
+    if (m > a.thr) {
+      ok = hub4<PARITY, WEIGHTED, SMALLR, true, PIX>(a, ws_g, e2, bk, h_even, h_odd, h_sum, i, m,
+                                                     &bar, phase, &s_row);
+    } else {
+      ok = hub4<PARITY, WEIGHTED, SMALLR, false, PIX>(a, ws_s, e2, bk, h_even, h_odd, h_sum, i,
+                                                      m, &bar, phase, &s_row);
+      if (WEIGHTED && ok) {
+        // the hub's sums times W_i into the global 192-bit sums (the
+        // barrier at the top of the loop orders the clearing before the
+        // next hub's additions)
+        const long long Wi = a.W[i];
+        for (int k = tid; k < nh; k += kThreads) {
+          unsigned long long* c = h_sum + 2 * nc * k;
+          unsigned long long elo = c[0], ehi = c[1], olo = 0, ohi = 0;
+          if (PARITY) {
+            // even = S0 + S+ + S-, odd = S+ - S- (each below 2^115 in
+            // magnitude, so no 128-bit overflow)
+            const unsigned long long plo = c[2], phi = c[3], nlo = c[4], nhi = c[5];
+            unsigned long long t = elo + plo;
+            ehi += phi + (t < elo ? 1ull : 0ull);
+            elo = t;
+            t = elo + nlo;
+            ehi += nhi + (t < elo ? 1ull : 0ull);
+            elo = t;
+            olo = plo - nlo;
+            ohi = phi - nhi - (plo < nlo ? 1ull : 0ull);
+            c[2] = c[3] = c[4] = c[5] = 0ull;
+          }
+          c[0] = c[1] = 0ull;
+          if (elo | ehi) fold_i128(a.weven + 3 * k, elo, ehi, Wi);
+          if (PARITY && (olo | ohi)) fold_i128(a.wodd + 3 * k, olo, ohi, Wi);
+        }
+      }
+    }
     if (!ok) return;
   }
   __syncthreads();
@@ -525,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
 size_t workspace_bytes(int mcap) {
   const size_t Wc = (size_t)(mcap + 31) / 32;
   return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + (size_t)mcap * Wc * 4 +
-         (size_t)mcap * 4 + (size_t)kWarps * ((mcap + 15) & ~15) + (size_t)kWarps * 64 * 5 + 64;
+         (size_t)mcap * 8 + (size_t)kWarps * ((mcap + 15) & ~15) + (size_t)kWarps * 64 * 5 + 64;
 }
 
 }  // namespace
@@ -591,6 +734,28 @@ const int8_t* pixel_sign_table(int* status) {
   return d;
 }
 
+// Orbit table relabelled to slots: orbit o becomes slot_of[o], flags kept.
+__global__ void k_relabel_lut(const uint32_t* __restrict__ lut, int64_t n,
+                              const int32_t* __restrict__ slot_of, uint32_t* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = lut[k];
+    out[k] = (e & 0xC0000000u) | (uint32_t)slot_of[e & 0x3FFFFFFFu];
+  }
+}
+
+// Per-slot results back to orbit order: dst[o] = src[slot_of[o]], `words`
+// 64-bit words per entry.
+__global__ void k_slots_to_orbits(const unsigned long long* __restrict__ src,
+                                  const int32_t* __restrict__ slot_of, int64_t n, int words,
+                                  unsigned long long* dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n * words;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = k / words;
+    dst[k] = src[(int64_t)slot_of[o] * words + (k - o * words)];
+  }
+}
+
 __global__ void k_dir_pixels(const int32_t* d, int64_t n, uint8_t* out) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -646,19 +811,19 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
                  : nullptr;
   a.W = weighted ? fw->d_W : nullptr;
   a.pixsign = pixsign;
-  a.weven = weighted ? (weven_out ? weven_out : sc.alloc<unsigned long long>(3 * (size_t)no))
-                     : nullptr;
-  a.wodd = (weighted && parity) ? (wodd_out ? wodd_out : sc.alloc<unsigned long long>(3 * (size_t)no))
-                                : nullptr;
+  a.hub_stride = 1;
+  // weighted results land in the callers' 192-bit arrays (or scratch)
+  unsigned long long* weven = weighted ? (weven_out ? weven_out : sc.alloc<unsigned long long>(3 * (size_t)no))
+                                       : nullptr;
+  unsigned long long* wodd = (weighted && parity) ? (wodd_out ? wodd_out : sc.alloc<unsigned long long>(3 * (size_t)no))
+                                                  : nullptr;
+  a.weven = weven;
+  a.wodd = wodd;
   a.hub_counter = sc.alloc<unsigned long long>(2);
   a.err = sc.alloc<int>(1);
   if (!a.hub_counter || !a.err || (parity && !a.odd) || (weighted && !a.weven) ||
       (weighted && parity && !a.wodd))
     return GS_ENOMEM;
-  cudaMemsetAsync(a.even, 0, sizeof(uint64_t) * no, s);
-  if (parity) cudaMemsetAsync(a.odd, 0, sizeof(uint64_t) * no, s);
-  if (a.weven) cudaMemsetAsync(a.weven, 0, sizeof(unsigned long long) * 3 * no, s);
-  if (a.wodd) cudaMemsetAsync(a.wodd, 0, sizeof(unsigned long long) * 3 * no, s);
   cudaMemsetAsync(a.hub_counter, 0, sizeof(unsigned long long) * 2, s);
   cudaMemsetAsync(a.err, 0, sizeof(int), s);
 
@@ -666,28 +831,63 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t hist_bytes = (size_t)no * 4 * (parity ? 2 : 1);
-  const size_t hist_aligned = (hist_bytes + 15) & ~(size_t)15;
-  // largest smem row that fits next to the histograms
-  int mcap = kMaxSmemRow;
   // static shared memory: the bucket table, the bin edges and a few words
   const size_t avail = (size_t)optin - 1024 - kBucketMax;
-  while (mcap > 32 && hist_aligned + workspace_bytes(mcap) > avail) mcap -= 32;
-  if (hist_aligned + workspace_bytes(mcap) > avail) return GS_ERANGE;
+  // bytes of one shared slot: unweighted, the even (and odd) count;
+  // weighted, one or three cells of a 128-bit sum and a count
+  const size_t per_slot = weighted ? (parity ? 60 : 20) : (parity ? 8 : 4);
+  // shared row capacity: the longest row rounded up to 32 (at most
+  // kMaxSmemRow), less while the slots do not fit
+  int mcap = std::min(kMaxSmemRow, std::max(32, (g.max_deg + 31) & ~31));
+  int nh = no;
+  if (!weighted) {
+    while (mcap > 32 && (size_t)no * per_slot + 16 + workspace_bytes(mcap) > avail) mcap -= 32;
+    if ((size_t)no * per_slot + 16 + workspace_bytes(mcap) > avail) return GS_ERANGE;
+  } else {
+    if (workspace_bytes(mcap) + 16 + per_slot > avail) return GS_ERANGE;
+    nh = (int)std::min<size_t>((size_t)no, (avail - workspace_bytes(mcap) - 16) / per_slot);
+    // variant 8: only 64 shared slots (exercises the global path of the
+    // other orbits on any input)
+    if (o.variant & 8) nh = std::min(nh, 64);
+  }
+  // with fewer slots than orbits the orbits are relabelled (most frequent
+  // first) and the per-slot results mapped back at the end
+  const bool relabel = nh < no;
+  unsigned long long* s_even = a.even;
+  unsigned long long* s_odd = a.odd;
+  int32_t* d_slot = nullptr;
+  uint32_t* d_lut2 = nullptr;
+  if (relabel) {
+    s_even = sc.alloc<unsigned long long>(no);
+    s_odd = parity ? sc.alloc<unsigned long long>(no) : nullptr;
+    a.weven = sc.alloc<unsigned long long>(3 * (size_t)no);
+    a.wodd = parity ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
+    d_slot = sc.alloc<int32_t>(no);
+    d_lut2 = sc.alloc<uint32_t>(t->lut.size());
+    if (!s_even || (parity && (!s_odd || !a.wodd)) || !a.weven || !d_slot || !d_lut2)
+      return GS_ENOMEM;
+  }
+  cudaMemsetAsync(s_even, 0, sizeof(uint64_t) * no, s);
+  if (parity) cudaMemsetAsync(s_odd, 0, sizeof(uint64_t) * no, s);
+  if (a.weven) cudaMemsetAsync(a.weven, 0, sizeof(unsigned long long) * 3 * no, s);
+  if (a.wodd) cudaMemsetAsync(a.wodd, 0, sizeof(unsigned long long) * 3 * no, s);
+  a.even = s_even;
+  a.odd = s_odd;
+  a.hot = nh;
 
   const bool small_r = g.edges[g.nb] < 32768;
-  auto pick = [&]() -> void (*)(Args) {
-#define GS_PICK(P, Wt, X)                                                    \
-  return small_r ? k_count4<P, Wt, true, X> : k_count4<P, Wt, false, X>
-    if (parity && pix) {
-      if (weighted) GS_PICK(true, true, true);
+  auto pick = [&](bool P, bool Wt, bool X) -> void (*)(Args) {
+#define GS_PICK(P_, Wt_, X_)                                                   \
+  return small_r ? k_count4<P_, Wt_, true, X_> : k_count4<P_, Wt_, false, X_>
+    if (P && X) {
+      if (Wt) GS_PICK(true, true, true);
       GS_PICK(true, false, true);
     }
-    if (parity) {
-      if (weighted) GS_PICK(true, true, false);
+    if (P) {
+      if (Wt) GS_PICK(true, true, false);
       GS_PICK(true, false, false);
     }
-    if (weighted) GS_PICK(false, true, false);
+    if (Wt) GS_PICK(false, true, false);
     GS_PICK(false, false, false);
 #undef GS_PICK
   };
@@ -695,8 +895,8 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   // input)
   const bool force_global = (o.variant & 1) != 0;
   const int thr = force_global ? 2 : mcap;
-  void (*kern)(Args) = pick();
-  const size_t smem = hist_aligned + workspace_bytes(mcap);
+  void (*kern)(Args) = pick(parity, weighted, pix);
+  const size_t smem = (size_t)nh * per_slot + 16 + workspace_bytes(mcap);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
@@ -728,8 +928,63 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
     a.gscratch = sc.alloc<unsigned char>(a.gscratch_stride * grid);
     if (!a.gscratch) return GS_ENOMEM;
   }
+
+  // Relabelling: count the tetrahedra of every orbit over an evenly strided
+  // sample of about 2048 hubs of the first window (unweighted, all slots in
+  // shared memory, long rows skipped), rank the orbits by that count and
+  // give the top nh the shared slots. Where that count kernel does not fit,
+  // the orbits keep their order. The choice changes only the speed.
+  auto relabel_orbits = [&](const Args& wa, cudaStream_t st_) -> int {
+    std::vector<int32_t> slot_of(no);
+    std::vector<int32_t> order(no);
+    for (int k = 0; k < no; ++k) order[k] = k;
+    const size_t smem_s = (size_t)no * 4 + 16 + workspace_bytes(mcap);
+    if (smem_s <= avail) {
+      unsigned long long* d_cnt = sc.alloc<unsigned long long>(no);
+      unsigned long long* d_hc = sc.alloc<unsigned long long>(1);
+      if (!d_cnt || !d_hc) return GS_ENOMEM;
+      cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * no, st_);
+      cudaMemsetAsync(d_hc, 0, sizeof(unsigned long long), st_);
+      Args sa = wa;
+      sa.big = nullptr;
+      sa.nbig = 0;
+      sa.thr = mcap;
+      sa.hot = no;
+      sa.lut = t->d_lut;
+      sa.even = d_cnt;
+      sa.odd = nullptr;
+      sa.weven = sa.wodd = nullptr;
+      sa.W = nullptr;
+      sa.hub_counter = d_hc;
+      sa.hub_stride = std::max<int64_t>(1, (wa.hub_end - wa.hub_begin) / 2048);
+      void (*ks)(Args) = pick(false, false, false);
+      cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
+      int ps = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, ks, kThreads, smem_s);
+      ks<<<std::max(1, ps) * sms, kThreads, smem_s, st_>>>(sa);
+      note_launch();
+      std::vector<unsigned long long> cnt(no);
+      cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(unsigned long long) * no, cudaMemcpyDeviceToHost,
+                      st_);
+      const cudaError_t e = cudaStreamSynchronize(st_);
+      if (e != cudaSuccess) return cuda_status(e);
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return cnt[x] > cnt[y]; });
+    }
+    for (int k = 0; k < no; ++k) slot_of[order[k]] = k;
+    cudaMemcpyAsync(d_slot, slot_of.data(), sizeof(int32_t) * no, cudaMemcpyHostToDevice, st_);
+    const int64_t nl = (int64_t)t->lut.size();
+    k_relabel_lut<<<(int)std::min<int64_t>((nl + 255) / 256, 4096), 256, 0, st_>>>(t->d_lut, nl,
+                                                                                  d_slot, d_lut2);
+    note_launch();
+    // the host vector must outlive the (pageable, hence synchronous) copy
+    const cudaError_t e = cudaStreamSynchronize(st_);
+    return e == cudaSuccess ? cuda_status(cudaGetLastError()) : cuda_status(e);
+  };
+
   KernelTimer timer(o.kernel_ms);
   timer.start(s);
+  bool first = true;
   st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
     a.adj = v.adj;
     a.adj_off = v.off1;
@@ -737,6 +992,12 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
     a.adj_off2 = v.off2;
     a.hub_begin = v.h0;
     a.hub_end = v.h1;
+    if (first && relabel) {
+      const int rs = relabel_orbits(a, s);
+      if (rs) return rs;
+      a.lut = d_lut2;
+    }
+    first = false;
     // the window's long rows go to the front of its hub queue
     std::vector<int64_t> big;
     if (g.max_deg > thr)
@@ -756,18 +1017,30 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
     return cuda_status(cudaGetLastError());
   });
   if (st) return st;
+  if (relabel) {
+    auto back = [&](const unsigned long long* src, int words, unsigned long long* dst) {
+      const int64_t n = (int64_t)no * words;
+      k_slots_to_orbits<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(src, d_slot,
+                                                                                     no, words, dst);
+      note_launch();
+    };
+    back(s_even, 1, reinterpret_cast<unsigned long long*>(d_even));
+    if (parity && d_odd) back(s_odd, 1, reinterpret_cast<unsigned long long*>(d_odd));
+    if (weighted) back(a.weven, 3, weven);
+    if (weighted && parity) back(a.wodd, 3, wodd);
+  }
   timer.stop(s);
   if (d_weven) {
     if (weighted)
-      { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(a.weven, no, 4 * fw->scale, d_weven); note_launch(); }
+      { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(weven, no, 4 * fw->scale, d_weven); note_launch(); }
     else
-      { k_u64_to_double<<<(no + 255) / 256, 256, 0, s>>>(a.even, no, d_weven); note_launch(); }
+      { k_u64_to_double<<<(no + 255) / 256, 256, 0, s>>>(reinterpret_cast<unsigned long long*>(d_even), no, d_weven); note_launch(); }
   }
   if (d_wodd && parity) {
     if (weighted)
-      { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(a.wodd, no, 4 * fw->scale, d_wodd); note_launch(); }
+      { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(wodd, no, 4 * fw->scale, d_wodd); note_launch(); }
     else
-      { k_i64_to_double<<<(no + 255) / 256, 256, 0, s>>>(reinterpret_cast<const long long*>(a.odd), no,
+      { k_i64_to_double<<<(no + 255) / 256, 256, 0, s>>>(reinterpret_cast<const long long*>(relabel ? d_odd : reinterpret_cast<int64_t*>(a.odd)), no,
                                                        d_wodd); note_launch(); }
   }
   int herr = 0;

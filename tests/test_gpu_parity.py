@@ -418,6 +418,46 @@ def test_4pcf_weighted(gs, torch_mod):
     assert np.array_equal(gwe, rwe) and np.array_equal(gwo, rwo)
 
 
+@pytest.fixture(scope="module")
+def many_orbits():
+    """8 bins (12,496 orbits, more than the weighted kernel keeps in shared
+    memory): clustered points with signed weights, and the oracle's sums."""
+    L = 100.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(12_000, L, seed=71, sigma=1.5, periodic=True)
+    X = oracle.quantize(pos, box_u, True)
+    rng = np.random.default_rng(72)
+    w = (catalogs.uniform_weights(len(X), seed=73) *
+         np.where(rng.random(len(X)) < 0.4, -1.0, 1.0)).astype(np.float32)
+    edges = catalogs.bin_edges_u(0.0, 9.0, 8)
+    og = oracle.Graph(X, box_u, edges)
+    return X, box_u, edges, w, og.count_4pcf(w), og.count_4pcf(w, pixel=True)
+
+
+@pytest.mark.parametrize("variant,windows", [(0, 0), (8, 0), (1, 0), (0, 3), (8, 3)])
+def test_4pcf_weighted_many_orbits(gs, torch_mod, many_orbits, variant, windows):
+    """Weighted sums with more orbits than shared slots: the orbits met most
+    often in a sample of hubs keep per-hub sums in shared memory, the rest go
+    to the global sums directly (variant 8 keeps only 64 slots, variant 1
+    sends every hub to the global path; windows > 0 samples the first row
+    window only)."""
+    X, box_u, edges, w, ref, _ = many_orbits
+    assert np.count_nonzero(ref[0]) > 1000 and np.abs(ref[1]).sum() > 0
+    g = gs.gs_build_graph(dev(torch_mod, X), box_u, edges, force_windows=windows)
+    got = gs.gs_count_4pcf_parity(g, dev(torch_mod, w), variant=variant)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.cpu().numpy(), b)
+
+
+@pytest.mark.parametrize("variant", [0, 8])
+def test_4pcf_pixel_weighted_many_orbits(gs, torch_mod, many_orbits, variant):
+    X, box_u, edges, w, _, ref = many_orbits
+    g = gs.gs_build_graph(dev(torch_mod, X), box_u, edges)
+    got = gs.gs_count_4pcf_parity_pix(g, dev(torch_mod, w), variant=variant)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.cpu().numpy(), b)
+
+
 @pytest.mark.parametrize("periodic", [True, False])
 def test_4pcf_global_workspace(gs, torch_mod, periodic):
     """variant 1 runs every hub in the launch whose workspace lives in global
