@@ -71,7 +71,8 @@ typedef struct {
    * 1, 2, 8, 16, 32 and 64, which select its paths. 1 = exercise the
    * long-row code paths on any input (the walk probes a hash of the hub row
    * staged in 64-word segments; gs_count_4pcf* keeps every hub's workspace in
-   * global memory). 2 = the walk reads hub rows from global memory
+   * global memory; gs_build_graph tests candidate pairs in 64-bit arithmetic
+   * even where 32 bits suffice). 2 = the walk reads hub rows from global memory
    * instead of staging them. 4 = gs_count_3pcf computes configuration
    * indices instead of looking them up in a shared table, and
    * gs_count_4pcf* bins the non-hub edges by binary search over the bin

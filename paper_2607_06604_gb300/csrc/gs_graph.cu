@@ -15,7 +15,8 @@ namespace gs {
 namespace {
 
 constexpr int kMaxCellsPerAxis = 256;
-constexpr int kBuildThreads = 256;
+constexpr int kCellThreads = 512;   // row pass: one CTA per cell
+constexpr int kCellCap = 4096;      // stencil points staged in shared memory (64 KB)
 
 struct GridDesc {
   int nc[3];
@@ -143,82 +144,151 @@ __device__ inline int warp_sort_asc(int v) {
   return v;
 }
 
-// Row pass: one warp per hub i visits the stencil cells with cell index
-// >= its own cell in increasing order and tests every point j > i.
-// FILL = false counts |N+(i)|; FILL = true writes the packed words.
-template <bool FILL>
-__global__ void __launch_bounds__(kBuildThreads) k_rows(
-    const int4* __restrict__ xyzp, int64_t n, GridDesc G, const int32_t* __restrict__ cell_start,
+// Squared minimum-image distance of a candidate pair, or a value >= E_nb^2
+// when the pair cannot be an edge. SMALL: E_nb <= 2^16 and every
+// coordinate difference fits 31 bits (box or extent below 2^30), so the
+// test runs in 32-bit arithmetic: a pair with any |component| >= 2^16 is no
+// edge, and otherwise each squared component is below 2^32.
+template <bool SMALL>
+__device__ inline int64_t cand_d2(const int4& P, const int4& Q, int64_t box, int64_t e2hi) {
+  if constexpr (SMALL) {
+    const int bx = (int)box;
+    auto mi32 = [bx](int d) {
+      if (bx) {
+        if (2 * d >= bx) d -= bx;
+        else if (2 * d < -bx) d += bx;
+      }
+      return d;
+    };
+    const unsigned ax = (unsigned)abs(mi32(Q.x - P.x)), ay = (unsigned)abs(mi32(Q.y - P.y)),
+                   az = (unsigned)abs(mi32(Q.z - P.z));
+    return (max(ax, max(ay, az)) >= 65536u)
+               ? e2hi
+               : (int64_t)((unsigned long long)(ax * ax) + (ay * ay) + (az * az));
+  } else {
+    const int64_t dx = min_image((int64_t)Q.x - P.x, box);
+    const int64_t dy = min_image((int64_t)Q.y - P.y, box);
+    const int64_t dz = min_image((int64_t)Q.z - P.z, box);
+    return dx * dx + dy * dy + dz * dz;
+  }
+}
+
+// Row pass, one CTA per cell (persistent over cells): every hub of a cell
+// has the same stencil, the cells with index >= its own (in increasing
+// order, so rows come out sorted). The CTA copies the points of those
+// cells into shared memory once (up to cap points; a cell whose stencil
+// holds more reads them from global memory), then each warp takes one hub
+// of the cell at a time and tests every candidate j > i.
+// FILL = false counts |N+(i)|; FILL = true writes the packed words. Only
+// hubs in [h0, h1) are processed (chunked out-of-core builds).
+template <bool FILL, bool SMALL>
+__global__ void __launch_bounds__(kCellThreads) k_rows_cells(
+    const int4* __restrict__ xyzp, GridDesc G, int64_t ncell, const int32_t* __restrict__ cell_start,
     const int32_t* __restrict__ cell_count, const int64_t* __restrict__ e2g, int nb,
     int32_t* deg, const int64_t* __restrict__ ptr, uint32_t* __restrict__ adj, int64_t h0,
-    int64_t h1, int64_t out_off) {
+    int64_t h1, int64_t out_off, int cap) {
+  extern __shared__ int4 s_cand[];
   __shared__ int64_t e2[kMaxBins + 1];
+  __shared__ int s_beg[27], s_cnt[27], s_off[28], s_cell[27];
+  __shared__ int s_ncell;
   for (int b = threadIdx.x; b <= nb; b += blockDim.x) e2[b] = e2g[b];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kW = kCellThreads / 32;
   const int64_t e2lo = e2[0], e2hi = e2[nb];
-  for (int64_t i = h0 + blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < h1;
-       i += warps) {
-    const int4 P = xyzp[i];
-    const int c0 = cell_axis(G, 0, P.x), c1 = cell_axis(G, 1, P.y), c2 = cell_axis(G, 2, P.z);
-    const int own = (c0 * G.nc[1] + c1) * G.nc[2] + c2;
-    int cell = INT_MAX;
-    if (lane < 27) {
-      int q[3] = {c0 + lane / 9 - 1, c1 + (lane / 3) % 3 - 1, c2 + lane % 3 - 1};
-      bool ok = true;
-      for (int a = 0; a < 3; ++a) {
-        if (G.box) q[a] = (q[a] + G.nc[a]) % G.nc[a];
-        else if (q[a] < 0 || q[a] >= G.nc[a]) ok = false;
+  for (int64_t own = blockIdx.x; own < ncell; own += gridDim.x) {
+    const int64_t cb = cell_start[own], ce = cb + cell_count[own];
+    const int64_t hb = cb > h0 ? cb : h0, he = ce < h1 ? ce : h1;
+    if (hb >= he) continue;  // the same decision in every thread
+    if (warp == 0) {
+      const int c2 = (int)(own % G.nc[2]), c1 = (int)((own / G.nc[2]) % G.nc[1]),
+                c0 = (int)(own / ((int64_t)G.nc[1] * G.nc[2]));
+      int cell = INT_MAX;
+      if (lane < 27) {
+        int q[3] = {c0 + lane / 9 - 1, c1 + (lane / 3) % 3 - 1, c2 + lane % 3 - 1};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+          if (G.box) q[a] = (q[a] + G.nc[a]) % G.nc[a];
+          else if (q[a] < 0 || q[a] >= G.nc[a]) ok = false;
+        }
+        if (ok) cell = (q[0] * G.nc[1] + q[1]) * G.nc[2] + q[2];
+        if (cell < own) cell = INT_MAX;
       }
-      if (ok) cell = (q[0] * G.nc[1] + q[1]) * G.nc[2] + q[2];
-      if (cell < own) cell = INT_MAX;
+      cell = warp_sort_asc(cell);
+      const int prev = __shfl_up_sync(0xffffffffu, cell, 1);
+      if (lane > 0 && prev == cell) cell = INT_MAX;  // duplicate stencil cell
+      cell = warp_sort_asc(cell);                    // valid cells first
+      const unsigned valid = __ballot_sync(0xffffffffu, cell != INT_MAX);
+      int c = 0;
+      if (cell != INT_MAX) {
+        s_cell[lane] = cell;
+        s_beg[lane] = cell_start[cell];
+        c = cell_count[cell];
+        s_cnt[lane] = c;
+      }
+      // exclusive offsets of the cells' points in the staged copy
+      int incl = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      if (lane < 27) s_off[lane + 1] = incl;
+      if (lane == 0) {
+        s_off[0] = 0;
+        s_ncell = __popc(valid);
+      }
     }
-    cell = warp_sort_asc(cell);
-    const int prev = __shfl_up_sync(0xffffffffu, cell, 1);
-    if (lane > 0 && prev == cell) cell = INT_MAX;  // duplicate stencil cell
-    int64_t count = 0;
-    int64_t out = FILL ? ptr[i] - out_off : 0;
-    for (int k = 0; k < 27; ++k) {
-      const int ck = __shfl_sync(0xffffffffu, cell, k);
-      if (ck == INT_MAX) continue;
-      const int b = cell_start[ck], e = b + cell_count[ck];
-      const int64_t s = (ck == own) ? i + 1 : b;
-      for (int64_t t0 = s; t0 < e; t0 += 32) {
-        const int64_t t = t0 + lane;
-        bool hit = false;
-        uint32_t word = 0;
-        if (t < e) {
-          const int4 Q = xyzp[t];
-          const int64_t dx = min_image((int64_t)Q.x - P.x, G.box);
-          const int64_t dy = min_image((int64_t)Q.y - P.y, G.box);
-          const int64_t dz = min_image((int64_t)Q.z - P.z, G.box);
-          const int64_t D2 = dx * dx + dy * dy + dz * dz;
-          if (D2 >= e2lo && D2 < e2hi) {
-            hit = true;
-            if (FILL) {
-              int lo = 0, hi = nb;
-              while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (e2[mid] <= D2) lo = mid;
-                else hi = mid;
+    __syncthreads();
+    const int ncs = s_ncell;
+    const bool staged = s_off[ncs] <= cap;
+    if (staged) {
+      for (int k = 0; k < ncs; ++k)
+        for (int t = threadIdx.x; t < s_cnt[k]; t += kCellThreads)
+          s_cand[s_off[k] + t] = xyzp[(int64_t)s_beg[k] + t];
+    }
+    __syncthreads();
+    for (int64_t i = hb + warp; i < he; i += kW) {
+      const int4 P = xyzp[i];
+      int64_t count = 0;
+      int64_t out = FILL ? ptr[i] - out_off : 0;
+      for (int k = 0; k < ncs; ++k) {
+        const int64_t b = s_beg[k], e = b + s_cnt[k];
+        const int64_t st = (s_cell[k] == own) ? i + 1 : b;
+        const int sk = s_off[k];
+        for (int64_t t0 = st; t0 < e; t0 += 32) {
+          const int64_t t = t0 + lane;
+          bool hit = false;
+          uint32_t word = 0;
+          if (t < e) {
+            const int4 Q = staged ? s_cand[sk + (int)(t - b)] : xyzp[t];
+            const int64_t D2 = cand_d2<SMALL>(P, Q, G.box, e2hi);
+            if (D2 >= e2lo && D2 < e2hi) {
+              hit = true;
+              if (FILL) {
+                int lo = 0, hi = nb;
+                while (hi - lo > 1) {
+                  const int mid = (lo + hi) >> 1;
+                  if (e2[mid] <= D2) lo = mid;
+                  else hi = mid;
+                }
+                word = ((uint32_t)t << 8) | (uint32_t)lo;
               }
-              word = ((uint32_t)t << 8) | (uint32_t)lo;
             }
           }
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (FILL && hit) adj[out + __popc(m & ((1u << lane) - 1u))] = word;
+          out += __popc(m);
+          count += __popc(m);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (FILL && hit) adj[out + __popc(m & ((1u << lane) - 1u))] = word;
-        out += __popc(m);
-        count += __popc(m);
+      }
+      if (!FILL) {
+        if (lane == 0) deg[i] = (int32_t)count;
+      } else {
+        const int64_t end = ptr[i + 1] - out_off;
+        for (int64_t p = out + lane; p < end; p += 32) adj[p] = kSentinel;
       }
     }
-    if (!FILL) {
-      if (lane == 0) deg[i] = (int32_t)count;
-    } else {
-      const int64_t end = ptr[i + 1] - out_off;
-      for (int64_t p = out + lane; p < end; p += 32) adj[p] = kSentinel;
-    }
+    __syncthreads();  // the staged copy is rewritten for the next cell
   }
 }
 
@@ -359,11 +429,28 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
   { k_scatter<<<grid_blocks(n, 256), 256, 0, s>>>(key, n, cursor, tmp); note_launch(); }
   { k_rank_in_cell<<<grid_blocks(n, 256), 256, 0, s>>>(key, tmp, n, start, cnt, d_xyz, g->d_xyzp); note_launch(); }
 
-  const int row_blocks = grid_blocks(n * 32, kBuildThreads);
+  // row passes: persistent CTAs over the cells
+  const size_t cell_smem = (size_t)kCellCap * sizeof(int4);
+  // 32-bit candidate tests when E_nb <= 2^16 and coordinate differences fit
+  // 31 bits
+  // (variant bit 1: the 64-bit test everywhere)
+  bool small = rmax <= 65536 && !(o.variant & 1);
+  for (int a = 0; a < 3 && small; ++a)
+    small = box_u ? box_u < (int64_t(1) << 30) : (int64_t)h[3 + a] - h[a] < (int64_t(1) << 30);
+  auto rows_count = small ? k_rows_cells<false, true> : k_rows_cells<false, false>;
+  auto rows_fill = small ? k_rows_cells<true, true> : k_rows_cells<true, false>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (auto k : {rows_count, rows_fill})
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cell_smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_fill, kCellThreads, cell_smem);
+  const int row_blocks = (int)std::min<int64_t>(ncell, (int64_t)std::max(1, per_sm) * sms * 8);
   KernelTimer timer(o.kernel_ms);
   timer.start(s);
-  { k_rows<false><<<row_blocks, kBuildThreads, 0, s>>>(g->d_xyzp, n, G, start, cnt, g->d_edges2, nb,
-                                                     g->d_deg, nullptr, nullptr, 0, n, 0); note_launch(); }
+  { rows_count<<<row_blocks, kCellThreads, cell_smem, s>>>(g->d_xyzp, G, ncell, start, cnt,
+                                                          g->d_edges2, nb, g->d_deg, nullptr,
+                                                          nullptr, 0, n, 0, kCellCap); note_launch(); }
   timer.stop(s);
   { k_pad_lengths<<<grid_blocks(n + 1, 256), 256, 0, s>>>(g->d_deg, n, len); note_launch(); }
   st = scan_exclusive_i64(len, g->d_ptr, n + 1, s, sc);
@@ -382,8 +469,9 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
     st = dev_alloc((void**)&g->d_adj, edge_bytes);
     if (st) return st;
     timer.start(s);
-    { k_rows<true><<<row_blocks, kBuildThreads, 0, s>>>(g->d_xyzp, n, G, start, cnt, g->d_edges2, nb,
-                                                      g->d_deg, g->d_ptr, g->d_adj, 0, n, 0); note_launch(); }
+    { rows_fill<<<row_blocks, kCellThreads, cell_smem, s>>>(g->d_xyzp, G, ncell, start, cnt,
+                                                           g->d_edges2, nb, g->d_deg, g->d_ptr,
+                                                           g->d_adj, 0, n, 0, kCellCap); note_launch(); }
     timer.stop(s);
     { k_graph_stats<<<grid_blocks(n * 32, 256), 256, 0, s>>>(g->d_deg, g->d_ptr, g->d_adj, 0, 0, n, tot,
                                                            tot + 1, (int*)(tot + 2)); note_launch(); }
@@ -414,8 +502,9 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
       const int64_t off = g->h_ptr[h0];
       const int64_t words = g->h_ptr[h1] - off;
       timer.start(s);
-      { k_rows<true><<<row_blocks, kBuildThreads, 0, s>>>(g->d_xyzp, n, G, start, cnt, g->d_edges2, nb,
-                                                        g->d_deg, g->d_ptr, stage, h0, h1, off); note_launch(); }
+      { rows_fill<<<row_blocks, kCellThreads, cell_smem, s>>>(g->d_xyzp, G, ncell, start, cnt,
+                                                             g->d_edges2, nb, g->d_deg, g->d_ptr,
+                                                             stage, h0, h1, off, kCellCap); note_launch(); }
       timer.stop(s);
       { k_graph_stats<<<grid_blocks((h1 - h0) * 32, 256), 256, 0, s>>>(g->d_deg, g->d_ptr, stage, off, h0, h1,
                                                                      tot, tot + 1, (int*)(tot + 2)); note_launch(); }

@@ -131,6 +131,9 @@ def test_graph_edges_bit_exact(gs, periodic):
         assert np.all(np.diff(r) > 0) and (len(r) == 0 or r[0] > i)
     info = gs.gs_graph_info(g)
     assert info["edges"] == len(ref) and info["max_degree"] == deg.max()
+    # variant 1: the 64-bit candidate test (the default here is the 32-bit one)
+    g64 = gs.gs_build_graph(X, bu, edges, variant=1)
+    assert np.array_equal(edge_set_from_gpu(gs, g64)[0], ref)
 
 
 # ----------------------------------------------------------------------------
