@@ -75,6 +75,8 @@ def _load():
     lib.or_config_bins.restype = ci
     lib.or_count_3pcf.argtypes = [P, P, P, P, i64, i64, ci]
     lib.or_count_3pcf.restype = ci
+    lib.or_count_3pcf_mu.argtypes = [P, P, ci, P, P, ci]
+    lib.or_count_3pcf_mu.restype = ci
     lib.or_count_4pcf.argtypes = [P, P, P, P, P, P, ci]
     lib.or_count_4pcf.restype = ci
     lib.or_pairs.argtypes = [P, P, P, P]
@@ -193,6 +195,21 @@ class Graph:
                                    int(hub_hi), self.nthreads)
         if st != 0:
             raise ValueError(f"oracle 3pCF failed ({st})")
+        return (counts, wsum) if w is not None else counts
+
+    def count_3pcf_mu(self, nmu: int, w=None):
+        """Anisotropic 3pCF: counts (and, with weights, exact weighted sums)
+        of shape [C(nb+2,3), nmu + 1] by configuration and mu bin of the
+        triangle's normal against the z axis; bin nmu holds the collinear
+        triangles."""
+        nc = num_configs(3, self.nb)
+        counts = np.zeros((nc, nmu + 1), dtype=np.uint64)
+        wsum = np.zeros((nc, nmu + 1), dtype=np.float64) if w is not None else None
+        wa = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        st = _load().or_count_3pcf_mu(self._h, _ptr(wa), int(nmu), _ptr(counts), _ptr(wsum),
+                                      self.nthreads)
+        if st != 0:
+            raise ValueError(f"oracle mu-binned 3pCF failed ({st})")
         return (counts, wsum) if w is not None else counts
 
     def count_4pcf(self, w=None, pixel: bool = False):

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import functools
 import itertools
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -267,3 +268,36 @@ def count4_pixel(X, box_u, edges_u):
             if abs(V) >= 1e-9:
                 odd[k] += (1 if V > 0 else -1) * perm_sign(p)
     return even, odd
+
+
+def count3_mu(X, box_u, edges_u, nmu, w=None):
+    """Anisotropic 3pCF by brute force: every triangle's mu is |n_z| / |n|
+    for the normal of its plane, taken here from the middle vertex j
+    (n = d(j, i) x d(j, k), the same line as from any vertex);
+    bin = floor(nmu mu) (at most nmu - 1) via integer square roots;
+    collinear triangles in bin nmu."""
+    nb = len(edges_u) - 1
+    B = bin_matrix(X, box_u, edges_u)
+    d = displacements(X, box_u)
+    conf = configs3(nb)
+    counts = np.zeros((len(conf), nmu + 1), dtype=np.uint64)
+    wsum = [[Fraction(0)] * (nmu + 1) for _ in conf]
+    n = X.shape[0]
+    for i, j, k in itertools.combinations(range(n), 3):
+        if B[i, j] < 0 or B[i, k] < 0 or B[j, k] < 0:
+            continue
+        u = [int(x) for x in d[j, i]]
+        v = [int(x) for x in d[j, k]]
+        nv = (u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0])
+        n2 = nv[0] ** 2 + nv[1] ** 2 + nv[2] ** 2
+        if n2 == 0:
+            m = nmu
+        else:
+            m = min(nmu - 1, math.isqrt((nmu * nmu * nv[2] * nv[2]) // n2))
+        c = conf[tuple(sorted((int(B[i, j]), int(B[i, k]), int(B[j, k]))))]
+        counts[c, m] += 1
+        if w is not None:
+            wsum[c][m] += Fraction(float(w[i])) * Fraction(float(w[j])) * Fraction(float(w[k]))
+    if w is None:
+        return counts
+    return counts, np.array([[float(x) for x in row] for row in wsum])

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "gs_oracle.cpp")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_rounding.py",
         "tests/test_oracle_tooling.py", "tests/test_oracle_connected.py",
-        "tests/test_oracle_pixel.py"]
+        "tests/test_oracle_pixel.py", "tests/test_oracle_mu.py"]
 
 # (name, text in the oracle, replacement)
 MUTANTS = [
@@ -46,6 +46,13 @@ MUTANTS = [
      "if (z_at_least(z, n2, k - 7)) ++band;"),
     ("pixel parity without the relabelling sign",
      "s = (Vp > 0 ? 1 : -1) * pi.sign;", "s = (Vp > 0 ? 1 : -1);"),
+    ("mu from the x component of the normal", "(i128)nmu * nmu * (nz * nz)",
+     "(i128)nmu * nmu * (nx * nx)"),
+    ("mu bin edge on the wrong side", "while (m > 0 && (i128)m * m * n2 > ",
+     "while (m > 0 && (i128)m * m * n2 >= "),
+    ("collinear triangles in the first mu bin", "int m = nmu;  // collinear", "int m = 0;  // collinear"),
+    ("a cross-product term from the wrong side", "const i128 ny = (i128)u[2] * v[0] - (i128)u[0] * v[2];",
+     "const i128 ny = (i128)u[2] * v[0] - (i128)u[0] * v[1];"),
 ]
 
 
