@@ -282,6 +282,28 @@ int gs_count_3pcf_equilateral(const gs_graph* g, const float* w, uint64_t* count
                               const gs_options* options);
 
 /*
+ * gs_count_3pcf_mu - anisotropic 3pCF. The paper's conclusions name mu
+ * binning for redshift-space distortions without defining it; the reading
+ * here: the line of sight is the z axis (distant observer), a triangle's
+ * mu is |n_z| / |n| for the normal n of its plane (the same from every
+ * vertex), its bin m the largest in [0, nmu) with m / nmu <= mu (decided in
+ * exact integer arithmetic; mu = 1 falls in bin nmu - 1), and collinear
+ * triangles (n = 0) go to bin nmu. Summing over the nmu + 1 bins gives
+ * gs_count_3pcf.
+ *   w       NULL or float32 [n] weights (caller's order); magnitudes must
+ *           span at most about 2^5 (GS_EUNSUPPORTED otherwise).
+ *   nmu     1..64 mu bins.
+ *   counts  uint64 [C(nb+2,3)][nmu + 1], configuration-major as in
+ *           gs_count_3pcf; wsum NULL or float64 of the same shape (exact
+ *           sums of w_i w_j w_k rounded once; needs w).
+ * Host or device pointers; options->shard/shards split the hubs as for
+ * gs_count_3pcf. Errors: GS_EINVAL (NULL graph or counts, wsum without w,
+ * nmu outside 1..64), and as gs_count_3pcf.
+ */
+int gs_count_3pcf_mu(const gs_graph* g, const float* w, int32_t nmu, uint64_t* counts,
+                     double* wsum, const gs_options* options);
+
+/*
  * gs_count_4pcf - binned tetrahedron counts (Sec. 2.2, Sec. 3.1.1):
  * tetrahedra whose six pairs are all edges, one count per S4 orbit.
  *   counts uint64 [n_orbits], wsum NULL or float64 [n_orbits] (exact;

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "GSError", "Options", "GraphStats", "Graph", "gs_quantize", "gs_build_graph",
-    "gs_graph_info", "gs_graph_tri_words", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_3pcf_equilateral", "gs_count_4pcf",
+    "gs_graph_info", "gs_graph_tri_words", "gs_graph_export", "gs_count_3pcf", "gs_tune_3pcf", "gs_count_3pcf_noalloc", "gs_count_3pcf_batch", "gs_count_3pcf_equilateral", "gs_count_3pcf_mu", "gs_count_4pcf",
     "gs_count_4pcf_parity", "gs_count_4pcf_parity_pix", "gs_direction_pixels",
     "gs_disconnected_4pcf", "gs_connected_4pcf", "gs_config_mask_cm",
     "gs_rebin_3pcf", "gs_rebin_4pcf", "gs_num_configs", "gs_config_bins",
@@ -99,6 +99,7 @@ def _load():
         "gs_disconnected_4pcf": ([P, P, P, P, P, P, OP], ci),
         "gs_connected_4pcf": ([P, P, P, P, P, P, P, P, P, OP], ci),
         "gs_count_3pcf_equilateral": ([P, P, P, P, OP], ci),
+        "gs_count_3pcf_mu": ([P, P, ci, P, P, OP], ci),
         "gs_config_mask_cm": ([ci, P, P, ctypes.POINTER(i64), OP], ci),
         "gs_rebin_3pcf": ([ci, ci, P, P, P, P, P, OP], ci),
         "gs_rebin_4pcf": ([ci, ci, P, P, P, P, P, P, P, P, P, OP], ci),
@@ -413,6 +414,21 @@ def gs_count_3pcf_equilateral(g: Graph, w=None, like=None, **opts):
     o = _options(**opts)
     _check(_lib.gs_count_3pcf_equilateral(g.handle, _ptr(w), _ptr(counts), _ptr(wsum),
                                           ctypes.byref(o)), "gs_count_3pcf_equilateral")
+    return (counts, wsum) if w is not None else counts
+
+
+def gs_count_3pcf_mu(g: Graph, nmu: int, w=None, like=None, **opts):
+    """Anisotropic 3pCF: uint64 [n_conf, nmu + 1] counts by configuration and
+    mu bin of the triangle's normal against the z axis (the last bin holds
+    collinear triangles), and with w the exact weighted sums (float64, same
+    shape)."""
+    ref = like if like is not None else w
+    shape = (gs_num_configs(3, g.nb), int(nmu) + 1)
+    counts = _empty_like_input(ref, shape, np.uint64)
+    wsum = _empty_like_input(ref, shape, np.float64) if w is not None else None
+    o = _options(**opts)
+    _check(_lib.gs_count_3pcf_mu(g.handle, _ptr(w), int(nmu), _ptr(counts), _ptr(wsum),
+                                 ctypes.byref(o)), "gs_count_3pcf_mu")
     return (counts, wsum) if w is not None else counts
 
 

@@ -917,6 +917,34 @@ int gs_count_3pcf_equilateral(const gs_graph* G, const float* w, uint64_t* count
   return st;
 }
 
+int gs_count_3pcf_mu(const gs_graph* G, const float* w, int32_t nmu, uint64_t* counts,
+                     double* wsum, const gs_options* options) {
+  if (!G || !counts || (wsum && !w) || nmu < 1 || nmu > 64) return GS_EINVAL;
+  const Graph& g = G->g;
+  const Opts o = read_opts(options);
+  const int64_t ncell = num_conf3(g.nb) * (nmu + 1);
+  int st = GS_OK;
+  {
+    Scratch sc(o.stream);
+    FixedW fw;
+    if (w) {
+      st = prepare_weights(g, w, &fw, sc, o.stream);
+      if (st) return st;
+    }
+    uint64_t* dc = is_device_ptr(counts) ? counts : sc.alloc<uint64_t>(ncell);
+    double* dw = wsum ? (is_device_ptr(wsum) ? wsum : sc.alloc<double>(ncell)) : nullptr;
+    if (!dc || (wsum && !dw)) return GS_ENOMEM;
+    st = count3mu_device(g, w ? &fw : nullptr, nmu, dc, dw, o, sc);
+    OutBuf outs[2] = {{counts, dc, sizeof(uint64_t) * ncell}, {wsum, dw, sizeof(double) * ncell}};
+    for (auto& b : outs)
+      if (!st && b.user && b.dev != b.user)
+        st = cuda_status(cudaMemcpyAsync(b.user, b.dev, b.bytes, cudaMemcpyDeviceToHost, o.stream));
+    cudaError_t e = cudaStreamSynchronize(o.stream);
+    if (!st) st = cuda_status(e);
+  }
+  return st;
+}
+
 int gs_connected_4pcf(const gs_graph* G_dr, const float* w_signed, const gs_graph* G_r,
                       const float* w_r, double* xi, double* zeta_even, double* zeta_odd,
                       double* zeta_disc, double* zeta_conn, const gs_options* options) {

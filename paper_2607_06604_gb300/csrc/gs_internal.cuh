@@ -179,6 +179,11 @@ int build_graph_device(const int32_t* d_xyz, int64_t n, int64_t box_u,
 int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* d_wsum,
                   const Opts& o, Scratch& sc, bool equi = false,
                   unsigned long long* wacc_out = nullptr);
+// Anisotropic 3pCF (csrc/gs_mu.cu): counts [nconf][nmu + 1] by configuration
+// and mu bin of the triangle's normal against the z axis (bin nmu:
+// collinear); d_wsum NULL or the same shape (narrow weights only).
+int count3mu_device(const Graph& g, const FixedW* fw, int nmu, uint64_t* d_counts,
+                    double* d_wsum, const Opts& o, Scratch& sc);
 int count3_batch_device(const Graph* const* gr, int ng, const FixedW* fws, uint64_t* const* d_counts,
                         double* const* d_wsum, const Opts& o, Scratch& sc);
 // pix: the odd channel from pixelised spoke directions (parity only)
