@@ -510,8 +510,9 @@ def measure_4pcf(gs, torch, runs=2):
 
 def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
     """The rows beyond the core path, each timed with CUDA events after one
-    warm-up call: the equilateral 3pCF on the randoms' graph of the default
-    workload (beside the full 3pCF kernel time), the pixelised-direction
+    warm-up call: the equilateral and the anisotropic (mu-binned) 3pCF on the
+    randoms' graph of the default workload (beside the full 3pCF kernel
+    time), the pixelised-direction
     parity 4pCF on the 2e5-point 4pCF workload, the signed-weight connected
     4pCF on 1e5 data + 1e5 randoms, and the configuration tooling."""
     import ctypes
@@ -539,6 +540,14 @@ def measure_next(gs, torch, randoms, box_u, edges, count3_ms):
         "full_3pcf_kernel_ms": count3_ms,
         "alg_bytes_per_launch": 4 * words,
         "achieved_gbs": 4 * words / (km.value / 1e3) / 1e9 if km.value else None}
+    # anisotropic 3pCF: 10 mu bins of the triangle normal against the z axis
+    kmu = ctypes.c_double(0.0)
+    cmu, ms_mu = timed(lambda: gs.gs_count_3pcf_mu(g, 10, like=pos, kernel_ms=kmu))
+    tmu = float(cmu.sum().item())
+    out["anisotropic_3pcf"] = {
+        "workload": "3e6 uniform randoms, L=1000, rmax 40, 20 bins x 10 mu bins, unweighted",
+        "call_ms": ms_mu, "kernel_ms": kmu.value, "triangles": tmu,
+        "triangles_per_s": tmu / (ms_mu / 1e3), "full_3pcf_kernel_ms": count3_ms}
     g.close()
 
     # pixelised-direction parity 4pCF on the 2e5-point 4pCF workload
