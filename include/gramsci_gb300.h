@@ -270,8 +270,10 @@ void gs_plan_destroy(gs_plan* plan);
  * kernels in Sec. 3.5 and Sec. 4.8; the paper gives no definition). Here it
  * is the nb configurations whose three sides share one bin: counts[b] is the
  * number of triangles with all three pair separations in bin b, equal to the
- * full 3pCF's entry at configuration (b, b, b), computed by a kernel that
- * follows same-bin edges only.
+ * full 3pCF's entry at configuration (b, b, b). The default kernel groups
+ * each hub's neighbours by hub-edge bin and tests only the pairs within a
+ * group; options->variant bit 512 selects the merge-walk's instantiation,
+ * which follows same-bin edges only.
  *   w       NULL or float32 [n] weights (caller's order).
  *   counts  uint64 [nb]; wsum NULL or float64 [nb] (exact sums of
  *           w_i w_j w_k rounded once; needs w).

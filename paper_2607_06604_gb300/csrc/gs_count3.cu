@@ -1141,6 +1141,177 @@ __global__ void __launch_bounds__(kPThreads, 2) k_count3p(PArgs a) {
   flush();
 }
 
+// Equilateral configurations (b, b, b) by pair geometry: a triangle is
+// equilateral in this sense only when both hub edges share bin b, so the CTA
+// stages N+(i) grouped by the hub edge's bin (a counting sort in shared
+// memory) and tests only the pairs within a group, against the one range
+// [E_b, E_b+1). Counts go to per-CTA 32-bit histograms [nb]; weighted, W_j W_k
+// to the hub's 96-bit sums [nb] folded by W_i into the CTA's 128-bit sums,
+// as in the other triangle kernels.
+template <int WM>
+__global__ void __launch_bounds__(kPThreads, 2) k_equi3p(PArgs a) {
+  constexpr bool WEIGHTED = WM != kNone;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int4* s_stage = reinterpret_cast<int4*>(smem);
+  __shared__ int64_t s_e2[kMaxBins + 1];
+  __shared__ int s_cnt[kMaxBins + 1], s_cur[kMaxBins + 1];
+  __shared__ unsigned s_hist[kMaxBins];
+  __shared__ unsigned s_hacc[WEIGHTED ? 3 * kMaxBins : 1];
+  __shared__ unsigned long long s_whist[WEIGHTED ? 2 * kMaxBins : 1];
+  __shared__ int64_t s_hub;
+  __shared__ unsigned long long s_pending;
+  __shared__ int s_flush, s_next;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nb = a.nb;
+  for (int b = tid; b <= nb; b += kPThreads) s_e2[b] = a.e2g[b];
+  for (int b = tid; b < nb; b += kPThreads) {
+    s_hist[b] = 0u;
+    if (WEIGHTED) {
+      s_hacc[3 * b] = s_hacc[3 * b + 1] = s_hacc[3 * b + 2] = 0u;
+      s_whist[2 * b] = s_whist[2 * b + 1] = 0ull;
+    }
+  }
+  if (tid == 0) s_pending = 0;
+  __syncthreads();
+  const Cat c = a.one;
+
+  auto flush = [&]() {
+    for (int b = tid; b < nb; b += kPThreads) {
+      const unsigned v = s_hist[b];
+      if (v) {
+        atomicAdd(c.counts + b, (unsigned long long)v);
+        s_hist[b] = 0u;
+      }
+      if (WEIGHTED) {
+        const unsigned long long lo = s_whist[2 * b], hi = s_whist[2 * b + 1];
+        if (lo | hi) {
+          atomic_add_i192(c.wacc + 3 * b, lo, hi);
+          s_whist[2 * b] = s_whist[2 * b + 1] = 0ull;
+        }
+      }
+    }
+  };
+
+  for (;;) {
+    if (tid == 0) {
+      const int64_t i = c.hub_begin + (int64_t)atomicAdd(a.hub_counter, 1ull);
+      s_hub = i < c.hub_end ? i : -1;
+      s_flush = 0;
+      s_next = 0;
+      if (i < c.hub_end) {
+        const unsigned long long d = (unsigned long long)c.deg[i];
+        const unsigned long long need = d * (d - (d > 0)) / 2;
+        if (s_pending + need > 0xFFFFFFFFull) {
+          s_flush = 1;
+          s_pending = need;
+        } else {
+          s_pending += need;
+        }
+      }
+    }
+    for (int b = tid; b <= nb; b += kPThreads) s_cnt[b] = 0;
+    __syncthreads();
+    const int64_t i = s_hub;
+    if (i < 0) break;
+    if (s_flush) {
+      flush();
+      __syncthreads();
+    }
+    const int d = c.deg[i];
+    if (d < 2) {
+      __syncthreads();
+      continue;
+    }
+    const uint32_t* row = row_at(c.adj, c.ptr, i, c.adj_off, c.split, c.adj_off2);
+    const int4 P = c.xyzp[i];
+    int4* S = d > a.cap ? reinterpret_cast<int4*>(a.gscratch + (size_t)blockIdx.x * a.gstride)
+                        : s_stage;
+    uint8_t* G = reinterpret_cast<uint8_t*>(S + (d > a.cap ? d : a.cap));  // group of each entry
+    // counting sort of the row by hub-edge bin
+    for (int t = tid; t < d; t += kPThreads) atomicAdd(&s_cnt[edge_bin(row[t]) + 1], 1);
+    __syncthreads();
+    if (tid == 0) {
+      for (int b = 1; b <= nb; ++b) s_cnt[b] += s_cnt[b - 1];
+      for (int b = 0; b < nb; ++b) s_cur[b] = s_cnt[b];
+    }
+    __syncthreads();
+    for (int t = tid; t < d; t += kPThreads) {
+      const uint32_t w = row[t];
+      const uint32_t k = edge_id(w);
+      const int4 Q = c.xyzp[k];
+      const int pos = atomicAdd(&s_cur[edge_bin(w)], 1);
+      G[pos] = (uint8_t)edge_bin(w);
+      S[pos] = make_int4((int)min_image((int64_t)Q.x - P.x, c.box),
+                         (int)min_image((int64_t)Q.y - P.y, c.box),
+                         (int)min_image((int64_t)Q.z - P.z, c.box),
+                         WEIGHTED ? (int)c.W[k] : (int)edge_bin(w));
+    }
+    __syncthreads();
+    // warps take four rows ra0..ra0+3 at a time; the pairs (ra, rb) with rb
+    // later in ra's group are spread over the lanes as one list
+    for (;;) {
+      int ra0 = 0;
+      if (lane == 0) ra0 = atomicAdd(&s_next, 4);
+      ra0 = __shfl_sync(0xffffffffu, ra0, 0);
+      if (ra0 >= d - 1) break;
+      int nk = 0;  // partners of row ra0 + lane (lanes 0..3)
+      if (lane < 4 && ra0 + lane < d - 1) nk = s_cnt[G[ra0 + lane] + 1] - (ra0 + lane) - 1;
+      int pre = nk;
+      for (int o = 1; o < 4; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+      }
+      const int p0 = __shfl_sync(0xffffffffu, pre, 0), p1 = __shfl_sync(0xffffffffu, pre, 1),
+                p2 = __shfl_sync(0xffffffffu, pre, 2), T = __shfl_sync(0xffffffffu, pre, 3);
+      for (int t = lane; t < T; t += 32) {
+        const int k = (t >= p0 ? 1 : 0) + (t >= p1 ? 1 : 0) + (t >= p2 ? 1 : 0);
+        const int base = k == 0 ? 0 : (k == 1 ? p0 : (k == 2 ? p1 : p2));
+        const int ra = ra0 + k, rb = ra + 1 + (t - base);
+        const int b = G[ra];
+        const int4 Da = S[ra], Db = S[rb];
+        const int64_t x = (int64_t)Db.x - Da.x, y = (int64_t)Db.y - Da.y,
+                      z = (int64_t)Db.z - Da.z;
+        const int64_t D2 = x * x + y * y + z * z;
+        if (D2 < s_e2[b] || D2 >= s_e2[b + 1]) continue;
+        atomicAdd(&s_hist[b], 1u);
+        if constexpr (WEIGHTED) {
+          const long long xw = (long long)Da.w * Db.w;  // |.| < 2^60
+          const uint32_t x0 = (uint32_t)xw, x1 = (uint32_t)((unsigned long long)xw >> 32);
+          const uint32_t o0 = atomicAdd(&s_hacc[3 * b], x0);
+          const uint32_t a1 = x1 + ((o0 + x0 < o0) ? 1u : 0u);
+          uint32_t a2 = (xw < 0 ? 0xFFFFFFFFu : 0u) + ((a1 < x1) ? 1u : 0u);
+          if (a1) {
+            const uint32_t o1 = atomicAdd(&s_hacc[3 * b + 1], a1);
+            a2 += (o1 + a1 < o1) ? 1u : 0u;
+          }
+          if (a2) atomicAdd(&s_hacc[3 * b + 2], a2);
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (WEIGHTED) {
+      // the hub's 96-bit sums times W_i into the CTA's 128-bit sums
+      const int64_t Wi = c.W[i];
+      for (int b = tid; b < nb; b += kPThreads) {
+        const uint32_t l = s_hacc[3 * b], m = s_hacc[3 * b + 1], h = s_hacc[3 * b + 2];
+        if (!(l | m | h)) continue;
+        s_hacc[3 * b] = s_hacc[3 * b + 1] = s_hacc[3 * b + 2] = 0u;
+        const unsigned long long ml = ((unsigned long long)m << 32) | l;
+        const unsigned long long uw = (unsigned long long)Wi;
+        const unsigned long long plo = ml * uw;
+        unsigned long long phi = __umul64hi(ml, uw) - (Wi < 0 ? ml : 0ull);
+        phi += (unsigned long long)((long long)(int32_t)h * Wi);
+        const unsigned long long olo = s_whist[2 * b];
+        const unsigned long long nlo = olo + plo;
+        s_whist[2 * b] = nlo;
+        s_whist[2 * b + 1] += phi + ((nlo < olo) ? 1ull : 0ull);
+      }
+    }
+  }
+  __syncthreads();
+  flush();
+}
+
 template <bool BATCH>
 void (*pick_count3p(int wm, bool nonneg, bool lut, int bin))(PArgs) {
 #define GS_P2(W, L)                                                        \
@@ -1391,7 +1562,54 @@ int count3_device(const Graph& g, const FixedW* fw, uint64_t* d_counts, double* 
   const bool pair_ok = !equi && (o.variant & ~4) == 0 && g.max_deg <= kMaxSmemHistDeg;
   const PairLaunch PL = pair_ok ? pair_launch(g.nb, nconf, wm != kNone, use_lut, g.edges)
                                 : PairLaunch{};
-  if (PL.cap > 0) {
+  // equilateral configurations: pair geometry within hub-edge bin groups
+  // (variant bit 512 keeps the walk's EQUI instantiation)
+  const bool equi_pair = equi && !(o.variant & 512) && g.max_deg <= kMaxSmemHistDeg;
+  if (equi_pair) {
+    PArgs pa;
+    pa.one = a.one;
+    pa.cats = nullptr;
+    pa.base = nullptr;
+    pa.ncats = 0;
+    pa.nb = g.nb;
+    pa.nconf = nconf;
+    pa.use_lut = 0;
+    pa.bk_shift = pa.bk_n = 0;
+    pa.lin_c = 0.0f;
+    pa.e2g = g.d_edges2;
+    pa.hub_counter = a.hub_counter;
+    int per_sm_bytes = 0;
+    cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // two CTAs per SM: the staging buffer takes what the static arrays leave
+    const size_t budget = (size_t)per_sm_bytes / 2 - 1024 - 16 * 1024;
+    pa.cap = (int)std::min<size_t>(4096, budget / 17) & ~31;
+    const size_t smem = (size_t)pa.cap * 17;
+    void (*kern)(PArgs) = wm == kNone ? k_equi3p<kNone> : k_equi3p<kExact>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem);
+    const int grid = std::max(1, per_sm) * sms;
+    pa.gscratch = nullptr;
+    pa.gstride = 0;
+    if (g.max_deg > pa.cap) {
+      pa.gstride = ((size_t)g.max_deg * 17 + 255) & ~(size_t)255;
+      pa.gscratch = sc.alloc<unsigned char>(pa.gstride * grid);
+      if (!pa.gscratch) return GS_ENOMEM;
+    }
+    timer.start(s);
+    st = for_each_window(g, o, sc, [&](const WinView& v) -> int {
+      pa.one.adj = v.adj;
+      pa.one.adj_off = v.off1;
+      pa.one.split = v.split;
+      pa.one.adj_off2 = v.off2;
+      pa.one.hub_begin = v.h0;
+      pa.one.hub_end = v.h1;
+      cudaMemsetAsync(pa.hub_counter, 0, sizeof(unsigned long long), s);
+      { kern<<<grid, kPThreads, smem, s>>>(pa); note_launch(); }
+      return cuda_status(cudaGetLastError());
+    });
+    timer.stop(s);
+  } else if (PL.cap > 0) {
     PArgs pa;
     pa.one = a.one;
     pa.cats = nullptr;

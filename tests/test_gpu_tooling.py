@@ -148,9 +148,10 @@ def test_equilateral_matches_oracle_and_full_3pcf(gs, periodic):
     sel = diagonal(len(edges) - 1)
     assert np.array_equal(gc, fc[sel]) and np.array_equal(gw, fw[sel])
     assert np.array_equal(gs.gs_count_3pcf_equilateral(g), c)
-    # every launch path: hash of the hub row (1), hub rows from global memory
-    # (2), a 2 KB table (8), compacted weighted hits (32), prefetch ring (64)
-    for v in (1, 2, 8, 32, 64, 72):
+    # the merge-walk's instantiation (512) and every launch path of it: hash
+    # of the hub row (1), hub rows from global memory (2), a 2 KB table (8),
+    # compacted weighted hits (32), prefetch ring (64)
+    for v in (512, 513, 514, 520, 544, 576, 584):
         vc, vw = gs.gs_count_3pcf_equilateral(g, w, variant=v)
         assert np.array_equal(vc, c), v
         assert np.array_equal(vw, gw), v
@@ -176,6 +177,7 @@ def test_equilateral_long_rows(gs):
     fc = gs.gs_count_3pcf(g)
     gc = gs.gs_count_3pcf_equilateral(g)
     assert np.array_equal(gc, fc[diagonal(3)]) and gc.sum() > 0
+    assert np.array_equal(gs.gs_count_3pcf_equilateral(g, variant=512), gc)
     Xd = torch.from_numpy(X).cuda()
     gd = gs.gs_count_3pcf_equilateral(gs.gs_build_graph(Xd, box_u, edges), like=Xd)
     assert gd.is_cuda and np.array_equal(gd.cpu().numpy(), gc)
