@@ -406,13 +406,18 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
       if ((bra[c >> 5] >> (c & 31)) & 1u)
         brw[c] = (uint8_t)bin_of(d2<SMALLR>(da, w.disp[c]), e2, nb, bk, a.bk_shift);
     __syncwarp();
-    int qn = 0;
-    // process the first 32 queue entries (or all when draining)
+    // the warp's queue of (b, c) entries is a ring of 64 slots: entries
+    // [qh, qt) are pending; a drain takes the 32 (or, at the end of the row,
+    // all) oldest, one per lane
+    int qh = 0, qt = 0;
     auto drain = [&](bool all) {
-      while (qn >= 32 || (all && qn > 0)) {
-        const bool active = lane < qn;
-        const uint32_t e = active ? qbc[lane] : 0u;
-        __syncwarp();
+      if (qt - qh >= 32 || (all && qt > qh)) {
+        const int take = qt - qh < 32 ? qt - qh : 32;  // warp-uniform
+        const bool active = lane < take;
+        __syncwarp();  // the entries written by other lanes are visible
+        const uint32_t e = active ? qbc[(qh + lane) & 63] : 0u;
+        __syncwarp();  // read before any lane writes the next entries
+        qh += take;
         if (active) {
           const int sb = (int)(e >> 16), sc = (int)(e & 0xFFFFu);
           const int b12 = brw[sb];
@@ -504,17 +509,6 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
             }
           }
         }
-        if (qn >= 32) {  // keep the overflow (the queue holds at most 63)
-          const int rest = qn - 32;
-          uint32_t mv = 0;
-          if (lane < rest) mv = qbc[32 + lane];
-          __syncwarp();
-          if (lane < rest) qbc[lane] = mv;
-          __syncwarp();
-          qn = rest;
-        } else {
-          qn = 0;
-        }
       }
     };
     for (int wb0 = sa >> 5; wb0 < W; ++wb0) {
@@ -528,9 +522,10 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
           if (wc == (sb >> 5)) x &= ~((2u << (sb & 31)) - 1u);
           if (!x) continue;
           const bool set = (x >> lane) & 1u;
-          if (set) qbc[qn + __popc(x & ((1u << lane) - 1u))] = ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
-          qn += __popc(x);
-          __syncwarp();
+          if (set)
+            qbc[(qt + __popc(x & ((1u << lane) - 1u))) & 63] =
+                ((uint32_t)sb << 16) | (uint32_t)(wc * 32 + lane);
+          qt += __popc(x);  // at most 31 + 32 pending: the ring never overfills
           drain(false);
         }
       }
