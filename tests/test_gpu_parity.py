@@ -136,6 +136,23 @@ def test_graph_edges_bit_exact(gs, periodic):
     assert np.array_equal(edge_set_from_gpu(gs, g64)[0], ref)
 
 
+@pytest.mark.parametrize("periodic", [True, False])
+def test_graph_dense_cells_and_wide_bins(gs, periodic):
+    """A clump whose cell stencil holds more points than the row pass stages
+    in shared memory (4,096: those cells read their points from global
+    memory), and E_nb above 2^16 (the 64-bit candidate test)."""
+    rng = np.random.default_rng(17)
+    box_u = 400_000
+    X = np.concatenate([rng.integers(0, box_u, size=(6000, 3)),
+                        200_000 + rng.integers(-2000, 2001, size=(6000, 3))]).astype(np.int32)
+    bu = box_u if periodic else 0
+    for edges in (np.array([0, 1000, 3000, 6000], dtype=np.int64),
+                  np.array([0, 30_000, 70_000, 90_000], dtype=np.int64)):
+        g = gs.gs_build_graph(X, bu, edges)
+        got = edge_set_from_gpu(gs, g)[0]
+        assert np.array_equal(got, edge_set_from_oracle(oracle.Graph(X, bu, edges)))
+
+
 # ----------------------------------------------------------------------------
 # a3 triangles
 
