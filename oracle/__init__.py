@@ -3,8 +3,9 @@
 A plain, slow, obviously correct CPU implementation of the paper's
 definitions (graph of Sec. 2.1, enumeration of Sec. 2.2, merge-walk of
 Sec. 3.1, three-way walk of Eq. threeway, parity of Sec. 3.2 / Eq. volume,
-disconnected term of Sec. 3.3 / Eq. disc). It lives in ``gs_oracle.cpp`` and
-is loaded here with ctypes.
+disconnected term of Sec. 3.3 / Eq. disc, and the mu-binned 3pCF named in the
+conclusions, in the reading stated at ``or_count_3pcf_mu``). It lives in
+``gs_oracle.cpp`` and is loaded here with ctypes.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. The CUDA library never uses it, and

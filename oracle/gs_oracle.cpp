@@ -29,6 +29,9 @@
 //    V != 0 and the orbit is chiral (its representative is fixed by no odd
 //    permutation, so sign(V) does not depend on the relabelling chosen).
 //    Degenerate tetrahedra (V == 0, computed exactly) get zero odd weight.
+//  * mu binning (named in the conclusions, not defined): line of sight z;
+//    a triangle's mu = |n_z| / |n| for the normal n of its plane; bin =
+//    largest m < nmu with m^2 |n|^2 <= nmu^2 n_z^2; collinear: bin nmu.
 //  * Pairs and the disconnected term (Sec. 3.3, Eq. disc): pairs[b] counts
 //    unordered edges in bin b; xi[b] = pairs[b]/RR[b] - 1; zeta_disc of an
 //    orbit = xi(r01)xi(r23) + xi(r02)xi(r13) + xi(r03)xi(r12) on its
