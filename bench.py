@@ -86,7 +86,7 @@ def measured_peaks():
 KERNEL_VERSION = "k_count3p.v1"  # bump when k_count3 changes; stale captures then report null
 
 
-KERNEL4_VERSION = "k_count4.v4"  # likewise for k_count4
+KERNEL4_VERSION = "k_count4.v5"  # likewise for k_count4
 
 
 def _profile_values(name):

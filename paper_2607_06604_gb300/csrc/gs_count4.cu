@@ -282,11 +282,12 @@ struct Workspace {
   int* cid;           // caller index of each neighbour (pixelised parity)
   int* wv;            // weight of each neighbour (weighted sums)
   uint8_t* brow;      // per warp: bin(a, c) of its current row a, cap bytes each
+  uint8_t* prow;      // pixelised parity, per warp: pixel of D_c - D_a for row a
   uint32_t* queue;    // per-warp queue of (b, c) entries: kWarps x 64 words
   int cap;
 };
 
-__device__ inline Workspace carve(unsigned char* p, int cap) {
+__device__ inline Workspace carve(unsigned char* p, int cap, bool pix) {
   const int Wc = (cap + 31) / 32;
   Workspace w;
   w.row = reinterpret_cast<uint32_t*>(p);
@@ -301,6 +302,8 @@ __device__ inline Workspace carve(unsigned char* p, int cap) {
   p += (size_t)cap * 4;
   w.brow = reinterpret_cast<uint8_t*>(p);
   p += (size_t)kWarps * ((cap + 15) & ~15);
+  w.prow = reinterpret_cast<uint8_t*>(p);
+  if (pix) p += (size_t)kWarps * ((cap + 15) & ~15);
   w.queue = reinterpret_cast<uint32_t*>(p);
   w.cap = (cap + 15) & ~15;
   return w;
@@ -352,9 +355,12 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     const int4 Q = a.xyzp[id];
     // the fourth component carries the hub edge's bin, so one 128-bit load
     // gives a vertex's displacement and b_i,vertex
-    w.disp[k] = make_int4((int)mi((int64_t)Q.x - P.x, a.box), (int)mi((int64_t)Q.y - P.y, a.box),
-                          (int)mi((int64_t)Q.z - P.z, a.box), (int)edge_bin(row[k]));
-    if (PIX) w.cid[k] = Q.w;
+    const int dx = (int)mi((int64_t)Q.x - P.x, a.box), dy = (int)mi((int64_t)Q.y - P.y, a.box),
+              dz = (int)mi((int64_t)Q.z - P.z, a.box);
+    w.disp[k] = make_int4(dx, dy, dz, (int)edge_bin(row[k]));
+    // pixelised parity: the caller index (below 2^24) and, in the top byte,
+    // the pixel of the spoke from the hub
+    if (PIX) w.cid[k] = (int)((unsigned)Q.w | ((unsigned)dir_pixel(dx, dy, dz) << 24));
     if (WEIGHTED) w.wv[k] = (int)a.W[id];
   }
   __syncthreads();
@@ -402,9 +408,19 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
     // bin(a, c) of every edge (a, c) of the row, once per row: the triangle
     // loop and the drain read b_12 and b_13 from here
     uint8_t* brw = w.brow + (size_t)warp * w.cap;
+    // pixelised parity: the pixels of the spokes from a (to the hub and to
+    // every c of the row), used when a has the smallest caller index
+    uint8_t* prw = w.prow + (size_t)warp * w.cap;
+    int pneg = 0;
     for (int c = sa + 1 + lane; c < m; c += 32)
-      if ((bra[c >> 5] >> (c & 31)) & 1u)
-        brw[c] = (uint8_t)bin_of(d2<SMALLR>(da, w.disp[c]), e2, nb, bk, a.bk_shift);
+      if ((bra[c >> 5] >> (c & 31)) & 1u) {
+        const int4 dc = w.disp[c];
+        brw[c] = (uint8_t)bin_of(d2<SMALLR>(da, dc), e2, nb, bk, a.bk_shift);
+        if (PIX)
+          prw[c] = (uint8_t)dir_pixel((int64_t)dc.x - da.x, (int64_t)dc.y - da.y,
+                                      (int64_t)dc.z - da.z);
+      }
+    if (PIX) pneg = dir_pixel(-(int64_t)da.x, -(int64_t)da.y, -(int64_t)da.z);
     __syncwarp();
     // the warp's queue of (b, c) entries is a ring of 64 slots: entries
     // [qh, qt) are pending; a drain takes the 32 (or, at the end of the row,
@@ -435,19 +451,20 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
             if constexpr (PIX) {
               // the pixelised reading: the three spokes from the vertex with
               // the smallest caller index, taken in ascending caller order; a
-              // sorting network keeps the displacements (from the hub) and
-              // the parity of the reordering
-              int key[4] = {P.w, w.cid[sa], w.cid[sb], w.cid[sc]};
-              int4 D[4] = {make_int4(0, 0, 0, 0), da, db, dc};
+              // sorting network orders the vertices (0 = hub, 1 = a, 2 = b,
+              // 3 = c) and keeps the parity of the reordering
+              const int ca = w.cid[sa], cb = w.cid[sb], cc = w.cid[sc];
+              int key[4] = {P.w, ca & 0xFFFFFF, cb & 0xFFFFFF, cc & 0xFFFFFF};
+              int vx[4] = {0, 1, 2, 3};
               int par = 1;
               auto cx = [&](int u, int v) {
                 if (key[u] > key[v]) {
                   const int tk = key[u];
                   key[u] = key[v];
                   key[v] = tk;
-                  const int4 td = D[u];
-                  D[u] = D[v];
-                  D[v] = td;
+                  const int tv = vx[u];
+                  vx[u] = vx[v];
+                  vx[v] = tv;
                   par = -par;
                 }
               };
@@ -456,14 +473,27 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
               cx(0, 2);
               cx(1, 3);
               cx(1, 2);
+              auto disp_of = [&](int v) {
+                return v == 0 ? make_int4(0, 0, 0, 0) : (v == 1 ? da : (v == 2 ? db : dc));
+              };
+              const int o = vx[0];
+              const int4 D0 = disp_of(o);
               int px[3];
               bool zero = false;  // coincident points: no direction, degenerate
 #pragma unroll
               for (int t = 1; t <= 3; ++t) {
-                const int64_t x = (int64_t)D[t].x - D[0].x, y = (int64_t)D[t].y - D[0].y,
-                              z = (int64_t)D[t].z - D[0].z;
+                const int v = vx[t];
+                const int4 Dv = disp_of(v);
+                const int64_t x = (int64_t)Dv.x - D0.x, y = (int64_t)Dv.y - D0.y,
+                              z = (int64_t)Dv.z - D0.z;
                 zero = zero || (x == 0 && y == 0 && z == 0);
-                px[t - 1] = dir_pixel(x, y, z);
+                if (o == 0) {  // spokes from the hub
+                  px[t - 1] = (int)((unsigned)(v == 1 ? ca : (v == 2 ? cb : cc)) >> 24);
+                } else if (o == 1) {  // spokes from a
+                  px[t - 1] = v == 0 ? pneg : (int)prw[v == 2 ? sb : sc];
+                } else {
+                  px[t - 1] = dir_pixel(x, y, z);
+                }
               }
               sgn = zero ? 0 : par * pix_sign(a.pixsign, px[0], px[1], px[2]);
             } else {
@@ -561,10 +591,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   int* h_odd = reinterpret_cast<int*>(sp);
   sp += (PARITY && !WEIGHTED) ? (size_t)nh * 4 : 0;
   unsigned char* sws = reinterpret_cast<unsigned char*>(((uintptr_t)sp + 15) & ~(uintptr_t)15);
-  const Workspace ws_s = carve(sws, a.mcap);
+  const Workspace ws_s = carve(sws, a.mcap, PIX);
   const Workspace ws_g = carve(a.gscratch ? a.gscratch + (size_t)blockIdx.x * a.gscratch_stride
                                           : sws,
-                               a.gscratch ? a.gcap : a.mcap);
+                               a.gscratch ? a.gcap : a.mcap, PIX);
 
   for (int k = tid; k < nh * nc; k += kThreads) {
     h_even[k] = 0;
@@ -697,10 +727,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_count4(Args a) {
   flush();
 }
 
-size_t workspace_bytes(int mcap) {
+size_t workspace_bytes(int mcap, bool pix) {
   const size_t Wc = (size_t)(mcap + 31) / 32;
   return (size_t)pad_row(mcap) * 4 + (size_t)mcap * 16 + (size_t)mcap * Wc * 4 +
-         (size_t)mcap * 8 + (size_t)kWarps * ((mcap + 15) & ~15) + (size_t)kWarps * 64 * 5 + 64;
+         (size_t)mcap * 8 + (size_t)kWarps * ((mcap + 15) & ~15) * (pix ? 2 : 1) +
+         (size_t)kWarps * 64 * 5 + 64;
 }
 
 }  // namespace
@@ -873,11 +904,11 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   int mcap = std::min(kMaxSmemRow, std::max(32, (g.max_deg + 31) & ~31));
   int nh = no;
   if (!weighted) {
-    while (mcap > 32 && (size_t)no * per_slot + 16 + workspace_bytes(mcap) > avail) mcap -= 32;
-    if ((size_t)no * per_slot + 16 + workspace_bytes(mcap) > avail) return GS_ERANGE;
+    while (mcap > 32 && (size_t)no * per_slot + 16 + workspace_bytes(mcap, pix) > avail) mcap -= 32;
+    if ((size_t)no * per_slot + 16 + workspace_bytes(mcap, pix) > avail) return GS_ERANGE;
   } else {
-    if (workspace_bytes(mcap) + 16 + per_slot > avail) return GS_ERANGE;
-    nh = (int)std::min<size_t>((size_t)no, (avail - workspace_bytes(mcap) - 16) / per_slot);
+    if (workspace_bytes(mcap, pix) + 16 + per_slot > avail) return GS_ERANGE;
+    nh = (int)std::min<size_t>((size_t)no, (avail - workspace_bytes(mcap, pix) - 16) / per_slot);
     // variant 8: only 64 shared slots (exercises the global path of the
     // other orbits on any input)
     if (o.variant & 8) nh = std::min(nh, 64);
@@ -928,7 +959,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   const bool force_global = (o.variant & 1) != 0;
   const int thr = force_global ? 2 : mcap;
   void (*kern)(Args) = pick(parity, weighted, pix);
-  const size_t smem = (size_t)nh * per_slot + 16 + workspace_bytes(mcap);
+  const size_t smem = (size_t)nh * per_slot + 16 + workspace_bytes(mcap, pix);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
@@ -956,7 +987,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   a.gscratch = nullptr;
   a.gscratch_stride = 0;
   if (g.max_deg > thr) {
-    a.gscratch_stride = (workspace_bytes(a.gcap) + 255) & ~(size_t)255;
+    a.gscratch_stride = (workspace_bytes(a.gcap, pix) + 255) & ~(size_t)255;
     a.gscratch = sc.alloc<unsigned char>(a.gscratch_stride * grid);
     if (!a.gscratch) return GS_ENOMEM;
   }
@@ -970,7 +1001,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
     std::vector<int32_t> slot_of(no);
     std::vector<int32_t> order(no);
     for (int k = 0; k < no; ++k) order[k] = k;
-    const size_t smem_s = (size_t)no * 4 + 16 + workspace_bytes(mcap);
+    const size_t smem_s = (size_t)no * 4 + 16 + workspace_bytes(mcap, false);
     if (smem_s <= avail) {
       unsigned long long* d_cnt = sc.alloc<unsigned long long>(no);
       unsigned long long* d_hc = sc.alloc<unsigned long long>(1);
