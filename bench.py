@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-4pcf", action="store_true",
                     help="skip the secondary 4pCF + parity measurement")
     ap.add_argument("--profile", choices=["count3", "count3w", "count4", "count4w", "pairs",
-                                          "equi3w"],
+                                          "equi3w", "mu3"],
                     default=None,
                     help="run one small case of one kernel for an ncu capture (no JSON)")
     ap.add_argument("--variant", type=int, default=0,
@@ -747,7 +747,7 @@ def run_profile(args):
 
     import paper_2607_06604_gb300 as gs
     torch.cuda.set_device(0)
-    if args.profile in ("count3", "count3w", "pairs", "equi3w"):
+    if args.profile in ("count3", "count3w", "pairs", "equi3w", "mu3"):
         # 1e6 uniform points at the randoms' density (3e-3 per (h^-1 Mpc)^3),
         # rmax 40 in 20 bins: a 1.6 GB graph
         L = 693.0
@@ -763,6 +763,8 @@ def run_profile(args):
                 gs.gs_count_3pcf(g, w, variant=args.variant)
             elif args.profile == "equi3w":
                 gs.gs_count_3pcf_equilateral(g, w)
+            elif args.profile == "mu3":
+                gs.gs_count_3pcf_mu(g, 10, like=pos)
             else:
                 gs.gs_disconnected_4pcf(g, like=pos, zeta=False)
     else:

@@ -47,6 +47,7 @@ struct MArgs {
   int cap;        // neighbours staged in shared memory
   int bk_shift, bk_n;  // squared-distance buckets (bk_n = 0: binary search)
   int smem_hist;  // 1: shared histogram of nconf (nmu + 1) counts
+  int use_lut;    // 1: configuration ranks from a shared table over (b_ij, b_ik, b_jk)
   unsigned long long* counts;  // [nconf][nmu + 1]
   unsigned long long* wacc;    // [nconf][nmu + 1][3] 192-bit sums, or nullptr
   unsigned long long* hub_counter;
@@ -100,12 +101,15 @@ __device__ inline int mu_bin(long long nx, long long ny, long long nz, int nmu) 
   return m;
 }
 
-template <bool WEIGHTED>
+// SMALL: E_nb <= 2^16, so a pair with any |component| >= 2^16 is no edge
+// and otherwise each squared component fits 32 bits.
+template <bool WEIGHTED, bool SMALL>
 __global__ void __launch_bounds__(kMThreads, 2) k_count3mu(MArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   int4* s_stage = reinterpret_cast<int4*>(smem);
   int* s_w = reinterpret_cast<int*>(s_stage + a.cap);
   unsigned* hist = reinterpret_cast<unsigned*>(s_w + (WEIGHTED ? a.cap : 0));
+  uint16_t* s_lut = reinterpret_cast<uint16_t*>(hist + (a.smem_hist ? a.nconf * (a.nmu + 1) : 0));
   __shared__ int64_t s_e2[kMaxBins + 1];
   __shared__ uint8_t s_bk[kMBucketMax];
   __shared__ int64_t s_hub;
@@ -125,6 +129,9 @@ __global__ void __launch_bounds__(kMThreads, 2) k_count3mu(MArgs a) {
   }
   if (a.smem_hist)
     for (int k = tid; k < ncell; k += kMThreads) hist[k] = 0u;
+  if (a.use_lut)
+    for (int k = tid; k < nb * nb * nb; k += kMThreads)
+      s_lut[k] = (uint16_t)conf3_rank(k / (nb * nb), (k / nb) % nb, k % nb, nb);
   if (tid == 0) s_pending = 0;
   __syncthreads();
   const int64_t e2lo = s_e2[0], e2hi = s_e2[nb];
@@ -198,10 +205,20 @@ __global__ void __launch_bounds__(kMThreads, 2) k_count3mu(MArgs a) {
       if (ra >= d - 1) break;
       const int4 Da = S[ra];
       const int64_t Wia = WEIGHTED ? Wi * SW[ra] : 0;
+      const int abase = Da.w * nb * nb;
       for (int rb = ra + 1 + lane; rb < d; rb += 32) {
         const int4 Db = S[rb];
-        const int64_t x = (int64_t)Db.x - Da.x, y = (int64_t)Db.y - Da.y, z = (int64_t)Db.z - Da.z;
-        const int64_t D2 = x * x + y * y + z * z;
+        int64_t D2;
+        if constexpr (SMALL) {
+          const unsigned ax = (unsigned)abs(Db.x - Da.x), ay = (unsigned)abs(Db.y - Da.y),
+                         az = (unsigned)abs(Db.z - Da.z);
+          if (max(ax, max(ay, az)) >= 65536u) continue;
+          D2 = (int64_t)((unsigned long long)(ax * ax) + (ay * ay) + (az * az));
+        } else {
+          const int64_t x = (int64_t)Db.x - Da.x, y = (int64_t)Db.y - Da.y,
+                        z = (int64_t)Db.z - Da.z;
+          D2 = x * x + y * y + z * z;
+        }
         if (D2 < e2lo || D2 >= e2hi) continue;
         int lo;
         if (a.bk_n) {
@@ -216,7 +233,7 @@ __global__ void __launch_bounds__(kMThreads, 2) k_count3mu(MArgs a) {
             else hi = mid;
           }
         }
-        const int cf = conf3_rank(Da.w, Db.w, lo, nb);
+        const int cf = a.use_lut ? (int)s_lut[abase + Db.w * nb + lo] : conf3_rank(Da.w, Db.w, lo, nb);
         const long long nx = (long long)Da.y * Db.z - (long long)Da.z * Db.y;
         const long long ny = (long long)Da.z * Db.x - (long long)Da.x * Db.z;
         const long long nz = (long long)Da.x * Db.y - (long long)Da.y * Db.x;
@@ -273,7 +290,9 @@ int count3mu_device(const Graph& g, const FixedW* fw, int nmu, uint64_t* d_count
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  a.cap = kMCap;
+  // staging capacity: the longest row (rows above kMCap are staged in
+  // global memory)
+  a.cap = std::min(kMCap, std::max(32, (g.max_deg + 31) & ~31));
   // squared-distance buckets no wider than the narrowest bin
   a.bk_shift = 0;
   a.bk_n = 0;
@@ -292,10 +311,19 @@ int count3mu_device(const Graph& g, const FixedW* fw, int nmu, uint64_t* d_count
   }
   const size_t stage = (size_t)a.cap * (weighted ? 20 : 16);
   const size_t hist = (size_t)ncell * 4;
+  const size_t lut = ((size_t)g.nb * g.nb * g.nb * 2 + 15) & ~(size_t)15;
   const size_t avail = (size_t)optin - 8 * (kMaxBins + 1) - kMBucketMax - 256;
   a.smem_hist = stage + hist <= avail ? 1 : 0;
-  const size_t smem = stage + (a.smem_hist ? hist : 0);
-  void (*kern)(MArgs) = weighted ? k_count3mu<true> : k_count3mu<false>;
+  // the table too when two CTAs per SM still fit
+  int per_sm_bytes = 0;
+  cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t two = (size_t)per_sm_bytes / 2 - 1024 - 8 * (kMaxBins + 1) - kMBucketMax - 256;
+  const size_t base = stage + (a.smem_hist ? hist : 0);
+  a.use_lut = (a.smem_hist && base + lut <= two) ? 1 : 0;
+  const size_t smem = base + (a.use_lut ? lut : 0);
+  const bool small = g.edges[g.nb] <= 65536;
+  void (*kern)(MArgs) = weighted ? (small ? k_count3mu<true, true> : k_count3mu<true, false>)
+                                 : (small ? k_count3mu<false, true> : k_count3mu<false, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMThreads, smem);
