@@ -78,8 +78,9 @@ typedef struct {
    * gs_count_4pcf* bins the non-hub edges by binary search over the bin
    * edges instead of squared-distance buckets. 8 = gs_count_3pcf
    * limits its direct-address table to 2 KB (rows split at their largest id
-   * gap, or hashed), and weighted gs_count_4pcf* keeps only 64 orbits'
-   * sums in shared memory (the others go straight to the global sums). 16 = gs_count_3pcf gives each block's first staging
+   * gap, or hashed), and gs_count_4pcf* keeps only 64 orbits' counters
+   * in shared memory (the others go straight to the global counts and
+   * sums). 16 = gs_count_3pcf gives each block's first staging
    * wait no polls, so the call fails with GS_ETIMEOUT after the blocks have
    * let their copies land (tests of the failure path). 32 = weighted
    * gs_count_3pcf compacts each warp's hits before recording them. 64 =

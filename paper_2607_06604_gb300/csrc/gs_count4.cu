@@ -22,6 +22,12 @@
 // 64-bit atomics. Hubs with more than kMaxSmemRow neighbours run in a
 // second launch whose per-hub workspace lives in global scratch.
 //
+// When the per-orbit counters of every orbit do not fit in shared memory
+// beside the hub workspace (unweighted: many bins; weighted: see below),
+// shared memory holds the `hot` orbits only: the orbit tables are relabelled
+// so that the orbits met most often in a sample of hubs come first, and a
+// tetrahedron of any other orbit goes to the global counters directly.
+//
 // Weighted sums (exact, fixed-point W): the hub's sums of W_a W_b W_c are
 // kept per orbit in shared 128-bit words (32-bit limbs), one for
 // each sign of the volume so that a tetrahedron adds to one word only, and
@@ -903,31 +909,40 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   // kMaxSmemRow), less while the slots do not fit
   int mcap = std::min(kMaxSmemRow, std::max(32, (g.max_deg + 31) & ~31));
   int nh = no;
-  if (!weighted) {
-    while (mcap > 32 && (size_t)no * per_slot + 16 + workspace_bytes(mcap, pix) > avail) mcap -= 32;
-    if ((size_t)no * per_slot + 16 + workspace_bytes(mcap, pix) > avail) return GS_ERANGE;
+  // unweighted: every orbit's counts in shared memory when a row capacity of
+  // at least 256 leaves room for them; otherwise (and always when weighted)
+  // as many slots as fit beside the longest row's workspace
+  int mfit = mcap;
+  while (!weighted && mfit > 256 && (size_t)no * per_slot + 16 + workspace_bytes(mfit, pix) > avail)
+    mfit -= 32;
+  if (!weighted && (size_t)no * per_slot + 16 + workspace_bytes(mfit, pix) <= avail) {
+    mcap = mfit;
   } else {
     if (workspace_bytes(mcap, pix) + 16 + per_slot > avail) return GS_ERANGE;
     nh = (int)std::min<size_t>((size_t)no, (avail - workspace_bytes(mcap, pix) - 16) / per_slot);
-    // variant 8: only 64 shared slots (exercises the global path of the
-    // other orbits on any input)
-    if (o.variant & 8) nh = std::min(nh, 64);
   }
+  // variant 8: only 64 shared slots (exercises the global path of the other
+  // orbits on any input)
+  if (o.variant & 8) nh = std::min(nh, 64);
   // with fewer slots than orbits the orbits are relabelled (most frequent
   // first) and the per-slot results mapped back at the end
   const bool relabel = nh < no;
   unsigned long long* s_even = a.even;
   unsigned long long* s_odd = a.odd;
+  unsigned long long* const o_odd = a.odd;  // odd counts in orbit order (caller's or scratch)
   int32_t* d_slot = nullptr;
   uint32_t* d_lut2 = nullptr;
   if (relabel) {
     s_even = sc.alloc<unsigned long long>(no);
     s_odd = parity ? sc.alloc<unsigned long long>(no) : nullptr;
-    a.weven = sc.alloc<unsigned long long>(3 * (size_t)no);
-    a.wodd = parity ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
+    if (weighted) {
+      a.weven = sc.alloc<unsigned long long>(3 * (size_t)no);
+      a.wodd = parity ? sc.alloc<unsigned long long>(3 * (size_t)no) : nullptr;
+    }
     d_slot = sc.alloc<int32_t>(no);
     d_lut2 = sc.alloc<uint32_t>(t->lut.size());
-    if (!s_even || (parity && (!s_odd || !a.wodd)) || !a.weven || !d_slot || !d_lut2)
+    if (!s_even || (parity && !s_odd) || (weighted && (!a.weven || (parity && !a.wodd))) ||
+        !d_slot || !d_lut2)
       return GS_ENOMEM;
   }
   cudaMemsetAsync(s_even, 0, sizeof(uint64_t) * no, s);
@@ -1088,7 +1103,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
       note_launch();
     };
     back(s_even, 1, reinterpret_cast<unsigned long long*>(d_even));
-    if (parity && d_odd) back(s_odd, 1, reinterpret_cast<unsigned long long*>(d_odd));
+    if (parity) back(s_odd, 1, o_odd);
     if (weighted) back(a.weven, 3, weven);
     if (weighted && parity) back(a.wodd, 3, wodd);
   }
@@ -1103,7 +1118,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
     if (weighted)
       { k_i192_to_double<<<(no + 255) / 256, 256, 0, s>>>(wodd, no, 4 * fw->scale, d_wodd); note_launch(); }
     else
-      { k_i64_to_double<<<(no + 255) / 256, 256, 0, s>>>(reinterpret_cast<const long long*>(relabel ? d_odd : reinterpret_cast<int64_t*>(a.odd)), no,
+      { k_i64_to_double<<<(no + 255) / 256, 256, 0, s>>>(reinterpret_cast<const long long*>(o_odd), no,
                                                        d_wodd); note_launch(); }
   }
   int herr = 0;

@@ -424,6 +424,9 @@ def test_4pcf_parity_clustered(gs, torch_mod, periodic, nb, seed):
     g = gs.gs_build_graph(dev(torch_mod, X), bu, edges)
     be, bo = gs.gs_count_4pcf_parity(g, like=dev(torch_mod, np.zeros(1)), variant=4)
     assert np.array_equal(be.cpu().numpy(), re) and np.array_equal(bo.cpu().numpy(), ro)
+    # variant 8: 64 orbits in shared memory, the others counted in global memory
+    he, ho = gs.gs_count_4pcf_parity(g, like=dev(torch_mod, np.zeros(1)), variant=8)
+    assert np.array_equal(he.cpu().numpy(), re) and np.array_equal(ho.cpu().numpy(), ro)
 
 
 def test_4pcf_weighted(gs, torch_mod):
@@ -467,6 +470,30 @@ def test_4pcf_weighted_many_orbits(gs, torch_mod, many_orbits, variant, windows)
     got = gs.gs_count_4pcf_parity(g, dev(torch_mod, w), variant=variant)
     for a, b in zip(got, ref):
         assert np.array_equal(a.cpu().numpy(), b)
+
+
+def test_4pcf_ten_bins(gs, torch_mod):
+    """nb = 10 (45,475 orbits): more orbits than shared memory holds beside
+    the hub workspace, so both the unweighted and the weighted kernels keep
+    some orbits (the most frequent in a sample of hubs, or the first ones
+    where the sampling kernel does not fit) in shared memory and send the
+    others to the global counts and sums."""
+    L = 60.0
+    box_u = int(L * 1024)
+    pos = catalogs.neyman_scott(3000, L, seed=81, sigma=1.5, periodic=True)
+    X = oracle.quantize(pos, box_u, True)
+    w = catalogs.uniform_weights(len(X), seed=82)
+    edges = catalogs.bin_edges_u(0.0, 7.0, 10)
+    ref = oracle.Graph(X, box_u, edges).count_4pcf(w)
+    assert ref[0].sum() > 10_000
+    g = gs.gs_build_graph(dev(torch_mod, X), box_u, edges)
+    got = gs.gs_count_4pcf_parity(g, dev(torch_mod, w))
+    for a, b in zip(got, ref):
+        assert np.array_equal(a.cpu().numpy(), b)
+    like = dev(torch_mod, np.zeros(1))
+    e, o = gs.gs_count_4pcf_parity(g, like=like)
+    assert np.array_equal(e.cpu().numpy(), ref[0]) and np.array_equal(o.cpu().numpy(), ref[1])
+    assert np.array_equal(gs.gs_count_4pcf(g, like=like).cpu().numpy(), ref[0])
 
 
 @pytest.mark.parametrize("variant", [0, 8])
