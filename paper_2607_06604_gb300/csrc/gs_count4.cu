@@ -160,7 +160,9 @@ __host__ __device__ inline int dir_pixel(int64_t x, int64_t y, int64_t z) {
   int band = -1;
 #ifdef __CUDA_ARCH__
   {
-    const float fx = (float)x, fy = (float)y, fz = (float)z;
+    // the components fit 32 bits (displacements below 2^20): 32-bit
+    // conversions, not the FP64 pipe's 64-bit ones
+    const float fx = (float)(int)x, fy = (float)(int)y, fz = (float)(int)z;
     const float t = 8.0f * fz * rsqrtf(fx * fx + fy * fy + fz * fz);
     if (fabsf(t - rintf(t)) >= 0.0009765625f) {
       const int f = 8 + (int)floorf(t);

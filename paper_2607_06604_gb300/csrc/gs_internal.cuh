@@ -329,6 +329,15 @@ __device__ inline void mul_i128(long long a, long long b, long long* lo, long lo
   *hi = __mul64hi(a, b);
 }
 
+// An integer below 2^40 in magnitude to the nearest float without a 64-bit
+// integer conversion (on GB300 those run on the slow FP64 pipe): v = hi 2^16
+// + lo with 0 <= lo < 2^16, both halves convert exactly, and the fused
+// multiply-add rounds the exact sum once.
+__device__ inline float i40_to_float(long long v) {
+  const int hi = (int)(v >> 16), lo = (int)(v & 0xFFFF);
+  return fmaf((float)hi, 65536.0f, (float)lo);
+}
+
 // Canonical rank of the sorted bin triple of (x, y, z), Sec. 5.1 ordering.
 __device__ __host__ inline int conf3_rank(int x, int y, int z, int nb) {
   int a = x < y ? x : y, b = x < y ? y : x;

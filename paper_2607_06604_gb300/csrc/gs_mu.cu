@@ -75,8 +75,9 @@ __device__ inline bool le(const U128& a, const U128& b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
 }
 
-// mu bin of a normal (nx, ny, nz), components below 2^55 in magnitude: the
-// largest m in [0, nmu) with m^2 |n|^2 <= nmu^2 nz^2 (at most 2^124), nmu
+// mu bin of a normal (nx, ny, nz), components below 2^39 in magnitude (the
+// graph keeps E_nb below 2^19): the largest m in [0, nmu) with
+// m^2 |n|^2 <= nmu^2 nz^2 (at most 2^124), nmu
 // for n = 0. t = nmu |nz| / |n| in single precision carries a relative
 // error below 12 2^-24 (the conversions, three products, two sums, the
 // reciprocal square root's 2 ulp and two more products), so below 2^-14
@@ -84,7 +85,7 @@ __device__ inline bool le(const U128& a, const U128& b) {
 // floor(t) is the bin. Otherwise the exact comparisons decide.
 __device__ inline int mu_bin(long long nx, long long ny, long long nz, int nmu) {
   if ((nx | ny | nz) == 0) return nmu;
-  const float fx = (float)nx, fy = (float)ny, fz = (float)nz;
+  const float fx = i40_to_float(nx), fy = i40_to_float(ny), fz = i40_to_float(nz);
   const float t = (float)nmu * fabsf(fz) * rsqrtf(fx * fx + fy * fy + fz * fz);
   const float r = rintf(t);
   if (fabsf(t - r) >= 0.0009765625f) {
