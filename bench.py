@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-4pcf", action="store_true",
                     help="skip the secondary 4pCF + parity measurement")
     ap.add_argument("--profile", choices=["count3", "count3w", "count4", "count4w", "pairs",
-                                          "equi3w", "mu3"],
+                                          "equi3w", "mu3", "count4pix"],
                     default=None,
                     help="run one small case of one kernel for an ncu capture (no JSON)")
     ap.add_argument("--variant", type=int, default=0,
@@ -782,6 +782,8 @@ def run_profile(args):
         for _ in range(2):
             if args.profile == "count4w":
                 gs.gs_count_4pcf_parity(g, w)
+            elif args.profile == "count4pix":
+                gs.gs_count_4pcf_parity_pix(g, like=pos)
             else:
                 gs.gs_count_4pcf_parity(g, like=pos)
     torch.cuda.synchronize()

@@ -357,7 +357,8 @@ int gs_count_4pcf_parity_pix(const gs_graph* g, const float* w, uint64_t* even, 
  * cos(theta) = z / |d| on [-1, 1] times 16 sectors of pi/8 in
  * phi = atan2(y, x) in [0, 2 pi); a direction on a band or sector edge
  * belongs to the band or sector above it; sector 0 on the z axis; pixel =
- * 16 band + sector. Decided exactly in integers on the device.
+ * 16 band + sector. Decided exactly on the device: single-precision
+ * estimates with error bounds, confirmed by integer comparisons near an edge.
  *   dirs    int32 [n][3] nonzero vectors (host or device), |components| < 2^20.
  *   pixels  uint8 [n] out (host or device).
  * Errors: GS_EINVAL, GS_ENOMEM, GS_ECUDA.

@@ -182,20 +182,35 @@ __host__ __device__ inline int dir_pixel(int64_t x, int64_t y, int64_t z) {
   int sector = 0;
   if (x != 0 || y != 0) {
     // turn by -pi/2 until the direction lies in [0, pi/2): a > 0, b >= 0
-    int quarter = 0;
-    int64_t a = x, b = y;
-    while (!(a > 0 && b >= 0)) {
-      const int64_t t = a;
-      a = b;
-      b = -t;
-      ++quarter;
+    int quarter;
+    int64_t a, b;
+    if (x > 0 && y >= 0) {
+      quarter = 0, a = x, b = y;
+    } else if (x <= 0 && y > 0) {
+      quarter = 1, a = y, b = -x;
+    } else if (x < 0 && y <= 0) {
+      quarter = 2, a = -x, b = -y;
+    } else {
+      quarter = 3, a = -y, b = x;
     }
+    // phi >= pi/8 iff b >= (sqrt 2 - 1) a, phi >= 3 pi/8 iff b >= (sqrt 2 + 1) a
+    // (never equal for integers, a > 0); on the device b - k a is formed in
+    // single precision (a, b below 2^21: error below 1/2) and decides when
+    // at least 1 from zero; otherwise, and on the host, the squared integer
+    // forms decide
+    int e1 = -1, e3 = -1;
+#ifdef __CUDA_ARCH__
+    if (a < (int64_t(1) << 21) && b < (int64_t(1) << 21)) {
+      const float fa = (float)(int)a, fb = (float)(int)b;
+      const float g1 = fmaf(-0.41421356237f, fa, fb), g3 = fmaf(-2.41421356237f, fa, fb);
+      if (fabsf(g1) >= 1.0f) e1 = g1 > 0.0f ? 1 : 0;
+      if (fabsf(g3) >= 1.0f) e3 = g3 > 0.0f ? 1 : 0;
+    }
+#endif
     const int64_t a2 = 2 * a * a;
-    int eighth = 0;
-    if ((a + b) * (a + b) >= a2) ++eighth;           // phi >= pi/8
-    if (b >= a) ++eighth;                            // phi >= pi/4
-    if (b > a && (b - a) * (b - a) >= a2) ++eighth;  // phi >= 3pi/8
-    sector = 4 * quarter + eighth;
+    if (e1 < 0) e1 = ((a + b) * (a + b) >= a2) ? 1 : 0;
+    if (e3 < 0) e3 = (b > a && (b - a) * (b - a) >= a2) ? 1 : 0;
+    sector = 4 * quarter + e1 + (b >= a ? 1 : 0) + e3;
   }
   return 16 * band + sector;
 }
@@ -481,28 +496,41 @@ __device__ bool hub4(const Args& a, const Workspace& w, const E2T* e2, const uin
               cx(0, 2);
               cx(1, 3);
               cx(1, 2);
-              auto disp_of = [&](int v) {
-                return v == 0 ? make_int4(0, 0, 0, 0) : (v == 1 ? da : (v == 2 ? db : dc));
-              };
+              // pixel of the spoke from the origin o to each vertex, and
+              // whether a spoke has zero length (coincident points)
               const int o = vx[0];
-              const int4 D0 = disp_of(o);
-              int px[3];
-              bool zero = false;  // coincident points: no direction, degenerate
-#pragma unroll
-              for (int t = 1; t <= 3; ++t) {
-                const int v = vx[t];
-                const int4 Dv = disp_of(v);
-                const int64_t x = (int64_t)Dv.x - D0.x, y = (int64_t)Dv.y - D0.y,
-                              z = (int64_t)Dv.z - D0.z;
-                zero = zero || (x == 0 && y == 0 && z == 0);
-                if (o == 0) {  // spokes from the hub
-                  px[t - 1] = (int)((unsigned)(v == 1 ? ca : (v == 2 ? cb : cc)) >> 24);
-                } else if (o == 1) {  // spokes from a
-                  px[t - 1] = v == 0 ? pneg : (int)prw[v == 2 ? sb : sc];
-                } else {
-                  px[t - 1] = dir_pixel(x, y, z);
-                }
+              int p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+              bool zero;
+              auto same = [](const int4& u, const int4& v) {
+                return u.x == v.x && u.y == v.y && u.z == v.z;
+              };
+              if (o == 0) {  // from the hub: cached with the caller indices
+                p1 = (int)((unsigned)ca >> 24);
+                p2 = (int)((unsigned)cb >> 24);
+                p3 = (int)((unsigned)cc >> 24);
+                zero = (da.x == 0 && da.y == 0 && da.z == 0) ||
+                       (db.x == 0 && db.y == 0 && db.z == 0) ||
+                       (dc.x == 0 && dc.y == 0 && dc.z == 0);
+              } else if (o == 1) {  // from a: the row's cached pixels
+                p0 = pneg;
+                p2 = prw[sb];
+                p3 = prw[sc];
+                zero = (da.x == 0 && da.y == 0 && da.z == 0) || same(db, da) || same(dc, da);
+              } else {  // from b or c: three pixelisations
+                const int4 Do = o == 2 ? db : dc, Dq = o == 2 ? dc : db;
+                const int q0 = dir_pixel(-(int64_t)Do.x, -(int64_t)Do.y, -(int64_t)Do.z);
+                const int q1 = dir_pixel((int64_t)da.x - Do.x, (int64_t)da.y - Do.y,
+                                         (int64_t)da.z - Do.z);
+                const int qq = dir_pixel((int64_t)Dq.x - Do.x, (int64_t)Dq.y - Do.y,
+                                         (int64_t)Dq.z - Do.z);
+                p0 = q0;
+                p1 = q1;
+                if (o == 2) p3 = qq;
+                else p2 = qq;
+                zero = (Do.x == 0 && Do.y == 0 && Do.z == 0) || same(da, Do) || same(Dq, Do);
               }
+              auto pix_of = [&](int v) { return v == 0 ? p0 : (v == 1 ? p1 : (v == 2 ? p2 : p3)); };
+              const int px[3] = {pix_of(vx[1]), pix_of(vx[2]), pix_of(vx[3])};
               sgn = zero ? 0 : par * pix_sign(a.pixsign, px[0], px[1], px[2]);
             } else {
               const int64_t V = det3<SMALLR>(da, db, dc);

@@ -32,6 +32,19 @@ def test_direction_pixels_bit_exact(gs):
                         rng.integers(-3, 4, size=(2000, 3)),
                         np.array([[12, 5, 0], [99, 41, 7], [-70, 29, -3], [1, 1, 0], [0, 0, 5],
                                   [0, 0, -5], [-4, 0, 0], [0, -4, 1], [3, -3, 3]])])
+    # directions within a fraction of a lattice unit of a sector edge (Pell
+    # approximations of tan(pi/8) = sqrt 2 - 1 and tan(3 pi/8) = sqrt 2 + 1,
+    # in every quadrant) and components up to the documented 2^20
+    pell = [(5, 2), (12, 5), (29, 12), (70, 29), (169, 70), (408, 169), (985, 408),
+            (2378, 985), (5741, 2378), (13860, 5741), (33461, 13860), (80782, 33461),
+            (195025, 80782), (470832, 195025)]
+    edge = []
+    for a_, b_ in pell:
+        for sx, sy in ((1, 1), (-1, 1), (-1, -1), (1, -1)):
+            for z_ in (0, 7, -11):
+                edge += [[sx * a_, sy * b_, z_], [sx * b_, sy * a_, z_]]
+    big = rng.integers(-(1 << 20) + 1, 1 << 20, size=(20_000, 3))
+    d = np.concatenate([d, np.array(edge), big])
     d = d[np.any(d != 0, axis=1)].astype(np.int32)
     ref = oracle.direction_pixels(d)
     assert np.array_equal(gs.gs_direction_pixels(d), ref)
