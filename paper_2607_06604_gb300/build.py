@@ -28,7 +28,11 @@ def nvcc() -> str:
 
 
 def common_flags() -> list[str]:
+    # host code: no fused multiply-add contraction (the FP64 pixel-volume
+    # table is defined as separately rounded operations; Arm compilers
+    # contract by default)
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "-Xcompiler", "-ffp-contract=off",
                    "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

@@ -79,7 +79,7 @@ struct Args {
   unsigned long long* weven;  // [n_orbits][3] 192-bit
   unsigned long long* wodd;
   const int64_t* __restrict__ W;
-  const int8_t* __restrict__ pixsign;  // pixelised parity: signs of sorted pixel triples
+  const uint8_t* __restrict__ pixsign;  // pixelised parity: 2-bit signs of sorted pixel triples
   unsigned long long* hub_counter;
   int* err;
   unsigned char* gscratch;  // per-CTA global workspace
@@ -217,16 +217,18 @@ __host__ __device__ inline int dir_pixel(int64_t x, int64_t y, int64_t z) {
 
 // Sign of the pixel volume (u_p1 x u_p2) . u_p3 of three pixel centres: 0
 // for repeated pixels, else the table entry of the sorted triple times the
-// parity of the sort. The table (host-built in FP64, 0 where |V| < 1e-9) is
-// indexed by the combinatorial number C(r,3) + C(q,2) + p of p < q < r.
-__device__ inline int pix_sign(const int8_t* __restrict__ T, int p1, int p2, int p3) {
+// parity of the sort. The table (host-built in FP64, 0 where |V| < 1e-9)
+// holds two bits per sorted triple p < q < r (1: positive, 2: negative, 0:
+// degenerate), entry C(r,3) + C(q,2) + p, four to a byte (690 KB).
+__device__ inline int pix_sign(const uint8_t* __restrict__ T, int p1, int p2, int p3) {
   if (p1 == p2 || p1 == p3 || p2 == p3) return 0;
   int s = 1;
   if (p1 > p2) { const int t = p1; p1 = p2; p2 = t; s = -s; }
   if (p2 > p3) { const int t = p2; p2 = p3; p3 = t; s = -s; }
   if (p1 > p2) { const int t = p1; p1 = p2; p2 = t; s = -s; }
   const int idx = p3 * (p3 - 1) * (p3 - 2) / 6 + p2 * (p2 - 1) / 2 + p1;
-  return s * (int)T[idx];
+  const int code = (T[idx >> 2] >> ((idx & 3) << 1)) & 3;
+  return s * ((code & 1) - (code >> 1));
 }
 
 // A 128-bit two's complement value (lo, hi) into a shared 128-bit sum kept
@@ -785,10 +787,10 @@ namespace {
 // 1e-9 in magnitude), built once on the host in FP64 and copied to each
 // device on first use.
 std::mutex g_pix_mu;
-std::vector<int8_t> g_pix_host;
-int8_t* g_pix_dev[64] = {nullptr};
+std::vector<uint8_t> g_pix_host;  // 2 bits per sorted triple
+uint8_t* g_pix_dev[64] = {nullptr};
 
-const int8_t* pixel_sign_table(int* status) {
+const uint8_t* pixel_sign_table(int* status) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) {
@@ -807,7 +809,7 @@ const int8_t* pixel_sign_table(int* status) {
       u[p][1] = rho * std::sin(phi);
       u[p][2] = zc;
     }
-    g_pix_host.resize((size_t)256 * 255 * 254 / 6);
+    g_pix_host.assign(((size_t)256 * 255 * 254 / 6 + 3) / 4, 0);
     size_t idx = 0;
     for (int r = 0; r < 256; ++r)
       for (int q = 0; q < r; ++q)
@@ -817,10 +819,11 @@ const int8_t* pixel_sign_table(int* status) {
           const double* c = u[r];
           const double v = (a[1] * b[2] - a[2] * b[1]) * c[0] + (a[2] * b[0] - a[0] * b[2]) * c[1] +
                            (a[0] * b[1] - a[1] * b[0]) * c[2];
-          g_pix_host[idx] = std::fabs(v) < 1e-9 ? 0 : (v > 0 ? 1 : -1);
+          const unsigned code = std::fabs(v) < 1e-9 ? 0u : (v > 0 ? 1u : 2u);
+          g_pix_host[idx >> 2] |= (uint8_t)(code << ((idx & 3) << 1));
         }
   }
-  int8_t* d = nullptr;
+  uint8_t* d = nullptr;
   cudaError_t e = cudaMalloc(&d, g_pix_host.size());
   if (e == cudaSuccess) e = cudaMemcpy(d, g_pix_host.data(), g_pix_host.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -877,7 +880,7 @@ int count4_device(const Graph& g, const FixedW* fw, bool parity, uint64_t* d_eve
   cudaStream_t s = o.stream;
   int st = GS_OK;
   pix = pix && parity;
-  const int8_t* pixsign = nullptr;
+  const uint8_t* pixsign = nullptr;
   if (pix) {
     pixsign = pixel_sign_table(&st);
     if (!pixsign) return st;
